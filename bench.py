@@ -1,0 +1,339 @@
+"""Throughput of the Cahn-Hilliard fine-grid step on GB300.
+
+Workload (default): drop in imposed shear on a 256 x 256 x 128 uniform mesh,
+x/y periodic on [0, 2], no-flux walls at z = 0, 1, u = (z - 1/2, 0, 0),
+Cn = 0.75 h, Pe = 0.9 / Cn, FP32 fields (the precision form), dt =
+min(0.9 dt_stab, CFL 0.5).  One step = one full RK3 step (three substeps of
+explicit RHS + x, y, z line solves) over every cell.  Metric: fine-grid
+cell-updates/s.  The working set (C, two H, rhs, three face velocities,
+~235 MB) exceeds the 129 MB L2, and L2 is also flushed between timed steps.
+
+``python bench.py [--gpus N --steps K --warmup W]`` prints one JSON line.
+``--impl reference`` times the CPU FP64 oracle instead (the slow baseline).
+Under torchrun every rank runs an independent replica of the workload
+(one box does not shard: replicas only); value = all ranks' cell updates
+divided by the max over ranks of the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="shear_drop_256x256x128", nx=256, ny=256, nz=128)
+# CPU sample for the oracle legs: the same workload recipe on a 128 x 128 x 64 mesh
+SAMPLE = dict(nx=128, ny=128, nz=64)
+METRIC = "fine-grid CH cell-updates/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def workload_inputs(nx, ny, nz):
+    from paper_2105_01865_gb300 import inputs, stability
+    f = inputs.shear_drop_box(nx, ny, nz)
+    h = f["h"]
+    dt = min(0.9 * stability.stable_dt(f["shape"], h, f["bc"], f["cn"], f["pe"]), 0.5 * h / 0.5)
+    f["dt"] = dt
+    return f
+
+
+# ---------------------------------------------------------------------------
+# oracle (CPU) legs, run in a fresh single-threaded interpreter
+# ---------------------------------------------------------------------------
+
+_ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+from oracle import ch_oracle as co
+import bench
+f = bench.workload_inputs({nx}, {ny}, {nz})
+nz, ny, nx = f["shape"]
+p = co.Params(nx, ny, nz, f["h"], cn=f["cn"], pe=f["pe"], dt=f["dt"], bc=f["bc"])
+C = f["C"]
+times = []
+for s in range({total}):
+    t0 = time.perf_counter()
+    C = co.step(C, f["vel"], p, 1)
+    times.append(time.perf_counter() - t0)
+print(json.dumps(dict(times=times, cells=nx * ny * nz)))
+"""
+
+
+def run_oracle(steps, warmup, sample=SAMPLE):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = _ORACLE_SNIPPET.format(root=ROOT, total=steps + warmup, **sample)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT)
+    if out.returncode != 0:
+        raise RuntimeError("oracle leg failed:\n" + out.stderr[-2000:])
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    t = r["times"][warmup:]
+    return r["cells"], t
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def reference_arm(args):
+    rank, world, _ = _rank()
+    if rank != 0:
+        return
+    cells, times = run_oracle(args.steps, args.warmup)
+    sec = sum(times)
+    value = cells * len(times) / sec
+    line = dict(metric=METRIC, value=value, unit="cell-updates/s", n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1e3 * sec / len(times), higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload=WORKLOAD["name"], global_batch=1, seq_len=0, parallelism="replicas"),
+                cpu_baseline=dict(value=value, unit="cell-updates/s", cores=1, kind="oracle",
+                                  sample=f"FP64 numpy oracle, one RK3 step per timed step of the same shear-drop "
+                                         f"recipe on a {SAMPLE['nx']}x{SAMPLE['ny']}x{SAMPLE['nz']} mesh, "
+                                         f"single thread, host CPU {cpu_model()}"),
+                e2e=dict(value=value, unit="cell-updates/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0),
+                gpu_launches=0)
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["no samples"])
+        return dict(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax), reasons=sorted(reasons), samples=len(sm))
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        for k in ("hbm_gbs", "hbm_GBps", "hbm"):
+            if k in d:
+                v = d[k]
+                return float(v["value"] if isinstance(v, dict) else v), "measured"
+    except (OSError, ValueError, KeyError, TypeError):
+        pass
+    return 6800.0, "fallback"
+
+
+def gpu_arm(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2105_01865_gb300 import build
+    from paper_2105_01865_gb300.solver import Solver
+    from paper_2105_01865_gb300 import capi
+
+    rank, world, local = _rank()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    capi.load()
+
+    W = WORKLOAD
+    f = workload_inputs(W["nx"], W["ny"], W["nz"])
+    ncell = W["nx"] * W["ny"] * W["nz"]
+
+    def make(prec):
+        s = Solver(f["shape"], f["h"], f["bc"], f["cn"], f["pe"], f["dt"], f["C"], precision=prec, advect=True,
+                   device=dev)
+        s.set_velocity_fine(*f["vel"])
+        return s
+
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def timed(s, steps, warmup, per_step=None):
+        """Sum of per-step CUDA-event durations on the solver's stream; L2
+        flushed between steps, outside the events."""
+        st = s.stream
+        for _ in range(warmup):
+            s.step(1)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        barrier()
+        with torch.cuda.stream(st):
+            for a, b in ev:
+                flush.fill_(1)
+                a.record(st)
+                (per_step or s.step)(1)
+                b.record(st)
+        barrier()
+        return sum(a.elapsed_time(b) for a, b in ev) / 1e3
+
+    # main FP32 line
+    s32 = make("f32")
+    with ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local) as clk:
+        sec = timed(s32, args.steps, args.warmup)
+    clocks = clk.summary()
+    s32.sync()
+    sec_t = torch.tensor([sec], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(sec_t, op=dist.ReduceOp.MAX)
+    sec = float(sec_t)
+    value = ncell * args.steps * world / sec
+
+    # per-kernel durations (events around every launch), same L2 flush between steps
+    ksum = [0.0] * 4
+    kreps = max(3, min(args.steps, 10))
+    for _ in range(kreps):
+        flush.fill_(1)
+        torch.cuda.synchronize(dev)
+        ms = capi.ch_profile_step(s32.handle, 1)
+        ksum = [a + b for a, b in zip(ksum, ms)]
+    kms = [x / kreps for x in ksum]
+    # algorithmic bytes per cell of one launch (FP32): explicit averages the
+    # three substeps (24, 28, 28 B), x/y solves 8 B, z solve + update 12 B
+    kbytes = [80.0 / 3.0, 8.0, 8.0, 12.0]
+    names = ["ch_explicit_rhs", "ch_solve_x", "ch_solve_y", "ch_solve_z_update"]
+    top = max(range(4), key=lambda k: kms[k])
+    peak, peak_src = measured_peak_hbm()
+    achieved = kbytes[top] * ncell / (kms[top] * 1e-3) / 1e9
+    roofline = dict(bound="hbm", kernel=names[top], achieved=achieved, peak=peak, unit="GB/s",
+                    frac=achieved / peak, traffic=None, peak_source=peak_src,
+                    kernels={n: dict(ms=m, algo_bytes_per_cell=b, gbs=b * ncell / (m * 1e-3) / 1e9)
+                             for n, m, b in zip(names, kms, kbytes)})
+
+    # end to end through the public API with host buffers: pinned H2D of C,
+    # one step, D2H of C, every step
+    hostC = torch.from_numpy(f["C"].astype("float32")).pin_memory()
+    outC = torch.empty_like(hostC).pin_memory()
+    s_e2e = make("f32")
+
+    def e2e_step(_n):
+        s_e2e.C.copy_(hostC, non_blocking=True)
+        s_e2e.step(1)
+        outC.copy_(s_e2e.C, non_blocking=True)
+
+    for _ in range(args.warmup):
+        with torch.cuda.stream(s_e2e.stream):
+            e2e_step(1)
+    sec_e2e = timed(s_e2e, args.steps, 0, per_step=e2e_step)
+    t = torch.tensor([sec_e2e], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e = dict(value=ncell * args.steps * world / float(t), unit="cell-updates/s",
+               h2d_bytes_per_step=ncell * 4, d2h_bytes_per_step=ncell * 4)
+
+    # the plain FP64 GPU step on the same workload, for the precision speedup
+    s64 = make("f64")
+    k64 = max(3, args.steps // 4)
+    sec64 = timed(s64, k64, min(args.warmup, 3))
+    fp64 = dict(ms_per_step=1e3 * sec64 / k64, value=ncell * k64 / sec64, unit="cell-updates/s",
+                fp32_speedup=(ncell * k64 / sec64) and (value / world) / (ncell * k64 / sec64))
+
+    line = dict(metric=METRIC, value=value, unit="cell-updates/s", n_gpus=world, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1e3 * sec / args.steps, higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+                config=dict(workload=W["name"], global_batch=world, seq_len=0,
+                            parallelism=f"replicas{world}", cells=ncell, precision="f32 fields, f64 reductions",
+                            l2="flushed between timed steps (256 MB write); working set 235 MB > L2"),
+                roofline=roofline, e2e=e2e, fp64_plain=fp64, clocks=clocks,
+                gpu_launches=args.steps * s32.launches_per_step())
+    if rank == 0 and not args.no_cpu_baseline:
+        cells, times = run_oracle(1, 0)
+        cpu_v = cells * len(times) / sum(times)
+        line["cpu_baseline"] = dict(value=cpu_v, unit="cell-updates/s", cores=1, kind="oracle",
+                                    sample=f"FP64 numpy oracle, one RK3 step of the same shear-drop recipe on a "
+                                           f"{SAMPLE['nx']}x{SAMPLE['ny']}x{SAMPLE['nz']} mesh, single thread, "
+                                           f"host CPU {cpu_model()}")
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for s in (s32, s_e2e, s64):
+        s.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

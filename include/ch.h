@@ -1,0 +1,175 @@
+/*
+ * ch.h -- C ABI of the GB300 Cahn-Hilliard fine-grid step library (libch.so).
+ *
+ * The library advances the volume fraction C of the phase-field method of
+ * "An efficient phase-field method for turbulent multiphase flows"
+ * (Liu, Ng, Chong, Lohse, Verzicco, arXiv 2105.01865) on a uniform fine mesh:
+ *
+ *   dC/dt + div(u C) = (1/Pe) [ -Cn^2 lap^2 C + lap(C^3 - 1.5 C^2 + 0.5 C) ]   (Sec. 2.1, Eq. eq-ch)
+ *
+ * with WENO5 advection and central lap(psi') treated explicitly by a
+ * low-storage RK3, and the biharmonic term replaced by A_x + A_y + A_z
+ * (Sec. 3.1, Eq. eq-a3d) treated by Crank-Nicolson in delta form with
+ * approximate factorisation into three pentadiagonal line solves
+ * (Eqs. eq-re, eq-fac, eq-fac-1..3).  It also transfers a face velocity from
+ * a stretched coarse mesh to the fine mesh (Sec. 3.4).
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns an int status (CH_OK = 0 or a CH_E* code below);
+ *    ch_error_string() names a code, ch_last_error() gives the handle's last
+ *    message.  On error nothing is enqueued after the failing launch.
+ *  - Fields are 3D arrays indexed [z][y][x], x fastest, contiguous, in the
+ *    handle's precision (float for CH_F32, double for CH_F64).  Face
+ *    velocities live on the staggered mesh: u on x-faces with nfx = nx
+ *    (periodic x) or nx + 1 (walls at x = 0 and x = nx h) planes, shape
+ *    [nz][ny][nfx]; v shape [nz][nfy][nx]; w shape [nfz][ny][nx].  Face f
+ *    lies between cells f - 1 and f.
+ *  - Device pointers passed in are BORROWED: the caller allocates them, keeps
+ *    them alive and unmodified by other work until the handle is freed (C and
+ *    the workspace) or until the call's work on the stream has completed (the
+ *    velocity inputs and outputs).  The library allocates only small tables
+ *    (LU factors, Hermite tables, reduction partials, a status word), freed
+ *    by ch_free().
+ *  - All work is enqueued on the stream given to ch_create (a cudaStream_t,
+ *    NULL = legacy default stream).  Only ch_mass, ch_free_energy, ch_sync
+ *    and ch_get_interp_tables wait for the stream.
+ */
+#ifndef CH_GB300_H
+#define CH_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define CH_OK 0
+#define CH_EINVAL 1      /* invalid argument or size (nothing was enqueued) */
+#define CH_ECUDA 2       /* a CUDA runtime call failed; see ch_last_error() */
+#define CH_ENONFINITE 3  /* a NaN/Inf appeared in C since the last check */
+#define CH_ETIMEOUT 4    /* a bounded device-side wait gave up */
+#define CH_ENOMEM 5      /* workspace too small or a table allocation failed */
+
+/* boundary condition per direction (Sec. 3.1: "first and last rows are
+ * determined by boundary conditions") */
+#define CH_PERIODIC 0    /* wrap: cyclic pentadiagonal line solves */
+#define CH_NOFLUX 1      /* walls: mirror ghosts C_{-1-m} = C_m, zero wall flux */
+
+/* arithmetic precision of fields and kernels */
+#define CH_F32 0         /* float fields, float arithmetic; FP64 reductions */
+#define CH_F64 1         /* double everywhere (the plain method) */
+
+typedef struct ch_params {
+    int64_t nx, ny, nz;   /* fine cells per direction, each >= 5 */
+    double h;             /* uniform fine spacing (Sec. 3: same h in all directions) */
+    int32_t bc[3];        /* CH_PERIODIC / CH_NOFLUX for x, y, z */
+    int32_t precision;    /* CH_F32 or CH_F64 */
+    double cn;            /* Cahn number Cn (> 0) */
+    double pe;            /* Peclet number Pe (> 0); mobility M = 1/Pe */
+    double dt;            /* full RK3 step (> 0) */
+    double w;             /* biharmonic weight: A_d = (w Cn^2/h^4)[1,-4,6,-4,1]; 4 = Eq. eq-a3d as printed */
+    double weno_eps;      /* WENO5 regulariser (1e-6) */
+    int32_t advect;       /* 0: u = 0, no advection term; 1: advect with the fine face velocity */
+    int32_t reserved;     /* must be 0 */
+    /* optional coarse (Navier-Stokes) mesh for the velocity transfer; all 0/NULL if unused.
+     * Host arrays of face coordinates, read during ch_create only: xf has ncx+1 entries,
+     * starting at 0 and ending at nx*h (likewise y, z).  Any (stretched) spacing. */
+    int64_t ncx, ncy, ncz;
+    const double* xf_coarse;
+    const double* yf_coarse;
+    const double* zf_coarse;
+} ch_params;
+
+typedef struct ch_handle ch_handle;
+
+/* Bytes of device workspace ch_create needs for these parameters (the
+ * explicit terms H of two RK3 substeps, the right-hand side / increment of
+ * the factorised solve, the fine face velocity and, with a coarse mesh, the
+ * coarse face velocity).  Returns 0 for invalid parameters. */
+size_t ch_workspace_bytes(const ch_params* p);
+
+/* Create a solver for the fine mesh of p (Sec. 3).  C: device array
+ * [nz][ny][nx] holding the volume fraction, advanced in place by ch_step.
+ * work: device workspace of >= ch_workspace_bytes(p) bytes, 256-byte aligned.
+ * stream: cudaStream_t for all work.  Builds the LU factors of the line
+ * operators (I + (alpha_l dt M / 2) A_d) for the three RK3 substeps, and with
+ * a coarse mesh the Hermite index/weight tables (Sec. 3.4: "generated only
+ * once").  Errors: CH_EINVAL (sizes < 5, non-positive h/cn/pe/dt/w, bad bc,
+ * coarse faces not spanning the fine box, misaligned pointers), CH_ENOMEM,
+ * CH_ECUDA.  On success *out owns the tables until ch_free. */
+int ch_create(const ch_params* p, void* C, void* work, size_t work_bytes, void* stream, ch_handle** out);
+
+/* Release the library-owned tables and the handle (not C or the workspace). */
+int ch_free(ch_handle* h);
+
+/* Copy a fine face velocity (device arrays, shapes in the header comment)
+ * into the workspace, for cases that prescribe u on the fine mesh
+ * (e.g. an imposed shear).  Requires advect = 1.  Asynchronous. */
+int ch_set_velocity_fine(ch_handle* h, const void* u, const void* v, const void* w);
+
+/* Copy the coarse staggered face velocity into the workspace (Sec. 3.4: the
+ * "base mesh" velocity).  Shapes: uc [ncz][ncy][ncfx], vc [ncz][ncfy][ncx],
+ * wc [ncfz][ncy][ncx] with ncf = nc (periodic) or nc + 1 (walls).  For an
+ * exactly solenoidal fine field it must be discretely divergence-free.
+ * Requires a coarse mesh at create.  Asynchronous. */
+int ch_set_velocity_coarse(ch_handle* h, const void* uc, const void* vc, const void* wc);
+
+/* Sec. 3.4: coarse normal gradients du/dx, dv/dy, dw/dz at coarse cell
+ * centres -> tri-cubic Hermite (4 points per direction) to fine cell centres
+ * -> integration along x, y, z from the reference planes x = 0, y = 0, z = 0
+ * (2D Hermite of the coarse face plane there; zero at a wall) -> fine face
+ * velocity in the workspace.  Requires a coarse mesh.  Asynchronous. */
+int ch_interp_to_fine(ch_handle* h);
+
+/* Copy the workspace's fine face velocity out to device arrays (shapes as
+ * for ch_set_velocity_fine).  Asynchronous. */
+int ch_get_velocity_fine(ch_handle* h, void* u, void* v, void* w);
+
+/* Copy the Hermite table of direction dir (0 = x, 1 = y, 2 = z) to HOST
+ * arrays: start[n_fine_dir] (first of the 4 coarse nodes; wrapped index for
+ * periodic directions) and weights[n_fine_dir][4] (double).  Synchronous. */
+int ch_get_interp_tables(ch_handle* h, int dir, int32_t* start, double* weights);
+
+/* Advance C by nsteps full RK3 steps (three substeps each; Sec. 3 and
+ * Eqs. eq-re .. eq-fac-3).  Asynchronous; a non-finite C sets a device flag
+ * reported by the next ch_sync / ch_mass / ch_free_energy.  nsteps >= 0. */
+int ch_step(ch_handle* h, int64_t nsteps);
+
+/* Drop mass m = h^3 sum C in FP64 (Sec. 4.3: l_loss = (m_t - m_0)/m_0).
+ * Waits for the stream; *out is a host double.  CH_ENONFINITE if C holds a
+ * NaN/Inf. */
+int ch_mass(ch_handle* h, double* out);
+
+/* Free energy F = h^3 sum [psi(C) + (Cn^2/2) sum_d ((C_{+e_d} - C)/h)^2],
+ * psi = C^2 (C-1)^2 / 4 (Sec. 1; forward differences, zero across a wall),
+ * accumulated in FP64.  Waits for the stream; *out is a host double. */
+int ch_free_energy(ch_handle* h, double* out);
+
+/* Wait for the handle's stream and report (then clear) the non-finite flag. */
+int ch_sync(ch_handle* h);
+
+/* Number of kernel launches one ch_step(h, 1) enqueues. */
+int ch_launches_per_step(const ch_handle* h);
+
+/* Measurement aid: run nsteps full steps (the same kernels as ch_step, but
+ * launched directly instead of as a graph) with CUDA events recorded on the
+ * handle's stream around every launch, wait for the stream, and write the mean
+ * duration in milliseconds of one launch of each kernel class to ms_out[4]:
+ * [0] explicit right-hand side, [1] x-line solve, [2] y-line solve,
+ * [3] z-line solve + update (averaged over the three substeps).  nsteps >= 1.
+ * Errors: CH_EINVAL, CH_ECUDA. */
+int ch_profile_step(ch_handle* h, int64_t nsteps, double* ms_out);
+
+/* Static description of a status code. */
+const char* ch_error_string(int status);
+
+/* Message of the last error on this handle ("" if none; never NULL). */
+const char* ch_last_error(const ch_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CH_GB300_H */

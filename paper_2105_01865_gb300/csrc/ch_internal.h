@@ -1,0 +1,98 @@
+// Internal declarations shared by the translation units of libch.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <vector>
+
+#include "../../include/ch.h"
+
+namespace chg {
+
+constexpr int kRK = 3;  // RK3 substeps (Sec. 3)
+
+// Low-storage RK3 coefficients (Sec. 3 cites the scheme without printing it):
+// gamma, rho per substep; alpha = gamma + rho weights the Crank-Nicolson step.
+constexpr double kGamma[kRK] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
+constexpr double kRho[kRK] = {0.0, -17.0 / 60.0, -5.0 / 12.0};
+
+// Coefficients of one factorised line operator (I + c A_d) of one direction
+// and substep, stored in the handle's precision (device memory).
+struct LineCoefs {
+    const void* l1;    // LU sub-diagonal multipliers (row j, col j-1)
+    const void* l2;    // LU multipliers (row j, col j-2)
+    const void* u1;    // U first super-diagonal
+    const void* u2;    // U second super-diagonal
+    const void* dinv;  // 1 / U diagonal
+    const void* W;     // periodic only: [n][4] Woodbury left vectors
+    const void* Z;     // periodic only: [n][4] Woodbury right vectors
+    const void* S;     // periodic only: [4][4] capacitance inverse
+    int n;
+    int periodic;
+};
+
+}  // namespace chg
+
+struct ch_handle {
+    ch_params p;
+    int prec;           // CH_F32 / CH_F64
+    size_t esz;         // element size
+    int64_t n[3];       // nx, ny, nz
+    int64_t nf[3];      // face planes per direction
+    int64_t ncell;
+    cudaStream_t stream;
+    void* C;
+    // workspace regions
+    void* H[2];
+    void* r;
+    void* vel[3];
+    void* vel_c[3];     // coarse face velocity
+    void* grad_c[3];    // coarse normal gradients
+    int64_t nc[3];      // coarse cells
+    int64_t ncf[3];     // coarse face planes
+    // library-owned device memory
+    void* coef_buf;
+    chg::LineCoefs coefs[3][chg::kRK];
+    double* red_partials;
+    double* red_out;
+    unsigned int* status;
+    int red_blocks;
+    // multiple-resolution tables (device)
+    int32_t* mr_start[3];
+    double* mr_w[3];
+    double* mr_coords;  // device copy of coarse face coordinates (x, y, z concatenated)
+    // CUDA graph of one full step
+    cudaGraphExec_t graph;
+    int graph_ready;
+    int launches_per_step;
+    char err[512];
+};
+
+namespace chg {
+
+inline int fail(ch_handle* h, int code, const char* fmt, ...) {
+    if (h) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(h->err, sizeof(h->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+#define CHG_CUDA(h, call)                                                                  \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return chg::fail((h), CH_ECUDA, "%s failed: %s (%s:%d)", #call,                \
+                             cudaGetErrorString(e_), __FILE__, __LINE__);                  \
+    } while (0)
+
+// multi-resolution entry points implemented in ch_mr.cu
+int mr_build_tables(ch_handle* h, const double* xf, const double* yf, const double* zf);
+void mr_destroy(ch_handle* h);
+
+}  // namespace chg

@@ -1,0 +1,417 @@
+// Multiple-resolution velocity transfer (arXiv 2105.01865, Sec. 3.4): the
+// face velocity of a stretched coarse mesh is carried to the uniform fine
+// mesh of C through its face-normal gradients, a tri-cubic Hermite spline of
+// four points per direction (64-point stencil, tables built once), and an
+// integration along every fine line from a reference plane.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "ch_internal.h"
+
+using namespace chg;
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// ---------------------------------------------------------------------------
+// Tables: for every fine cell centre x = (i + 1/2) h of one direction, the
+// first of its four coarse nodes and the four weights of the cubic Hermite
+// segment that contains x.  Nodes are coarse cell centres; the base node is
+// the last node at or left of x; slopes are central differences over the
+// neighbouring nodes (one-sided at the ends of a walled direction, whose
+// stencil is clamped into the node range); periodic directions wrap.
+// ---------------------------------------------------------------------------
+__global__ void mr_tables_kernel(const double* __restrict__ faces, int nc, int periodic, int nfine, double h,
+                                 int32_t* __restrict__ start_out, double* __restrict__ w_out,
+                                 float* __restrict__ wf_out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nfine) return;
+    const double x = ((double)i + 0.5) * h;
+    const double P = faces[nc] - faces[0];
+    auto node = [&](int k) { return 0.5 * (faces[k] + faces[k + 1]); };
+    // j = max{j : node_j <= x}, -1 if none (binary search)
+    int lo = 0, hi = nc;  // invariant: node(lo-1) <= x < node(hi) in the extended sense
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (node(mid) <= x)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    const int j = lo - 1;
+    double wgt[4] = {0.0, 0.0, 0.0, 0.0};
+    int start;
+    double xs[4];
+    int a, b, la, ha, lb, hb;  // segment nodes and slope neighbours, as slots 0..3
+    if (periodic) {
+        start = ((j - 1) % nc + nc) % nc;
+        for (int m = 0; m < 4; ++m) {
+            const int k = j - 1 + m;
+            const int q = (k >= 0) ? k / nc : -((-k + nc - 1) / nc);
+            const int kk = k - q * nc;
+            xs[m] = node(kk) + P * (double)q;
+        }
+        a = 1; b = 2; la = 0; ha = 2; lb = 1; hb = 3;
+    } else {
+        const int seg = min(max(j, 0), nc - 2);
+        start = min(max(seg - 1, 0), nc - 4);
+        for (int m = 0; m < 4; ++m) xs[m] = node(start + m);
+        a = seg - start;
+        b = a + 1;
+        la = max(seg - 1, 0) - start;
+        ha = seg + 1 - start;
+        lb = seg - start;
+        hb = min(seg + 2, nc - 1) - start;
+    }
+    const double dx = xs[b] - xs[a];
+    const double t = (x - xs[a]) / dx;
+    const double h00 = 2 * t * t * t - 3 * t * t + 1;
+    const double h10 = t * t * t - 2 * t * t + t;
+    const double h01 = -2 * t * t * t + 3 * t * t;
+    const double h11 = t * t * t - t * t;
+    wgt[a] += h00;
+    wgt[b] += h01;
+    const double sa = h10 * dx / (xs[ha] - xs[la]);
+    wgt[ha] += sa;
+    wgt[la] -= sa;
+    const double sb = h11 * dx / (xs[hb] - xs[lb]);
+    wgt[hb] += sb;
+    wgt[lb] -= sb;
+    start_out[i] = start;
+    for (int m = 0; m < 4; ++m) {
+        w_out[4 * i + m] = wgt[m];
+        wf_out[4 * i + m] = (float)wgt[m];
+    }
+}
+
+// Step (1) of Sec. 3.4: normal gradients at coarse cell centres.
+template <typename T>
+__global__ void mr_gradients_kernel(const T* __restrict__ uc, const T* __restrict__ vc, const T* __restrict__ wc,
+                                    const double* __restrict__ xf, const double* __restrict__ yf,
+                                    const double* __restrict__ zf, int ncx, int ncy, int ncz, int ncfx, int ncfy,
+                                    int per_x, int per_y, int per_z, T* __restrict__ gx, T* __restrict__ gy,
+                                    T* __restrict__ gz) {
+    const int64_t N = (int64_t)ncx * ncy * ncz;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % ncx);
+        const int64_t t = e / ncx;
+        const int j = (int)(t % ncy), k = (int)(t / ncy);
+        const int ip = per_x ? (i + 1) % ncx : i + 1;
+        const int jp = per_y ? (j + 1) % ncy : j + 1;
+        const int kp = per_z ? (k + 1) % ncz : k + 1;
+        const T du = uc[((int64_t)k * ncy + j) * ncfx + ip] - uc[((int64_t)k * ncy + j) * ncfx + i];
+        const T dv = vc[((int64_t)k * ncfy + jp) * ncx + i] - vc[((int64_t)k * ncfy + j) * ncx + i];
+        const T dw = wc[((int64_t)kp * ncy + j) * ncx + i] - wc[((int64_t)k * ncy + j) * ncx + i];
+        gx[e] = du / T(xf[i + 1] - xf[i]);
+        gy[e] = dv / T(yf[j + 1] - yf[j]);
+        gz[e] = dw / T(zf[k + 1] - zf[k]);
+    }
+}
+
+template <typename T>
+struct Tab {
+    const int32_t* __restrict__ s;
+    const T* __restrict__ w;
+};
+
+// Step (2): the 64-point tri-cubic Hermite value of a coarse cell-centred
+// field at fine cell (i, j, k), contracted x first, then y, then z.
+template <typename T>
+__device__ __forceinline__ T hermite3(const T* __restrict__ G, int ncx, int ncy, int ncz, int sx, const T* wx,
+                                      int sy, const T* wy, int sz, const T* wz) {
+    T acc = T(0);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        int kz = sz + c;
+        kz -= (kz >= ncz) ? ncz : 0;
+        T accy = T(0);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            int ky = sy + b;
+            ky -= (ky >= ncy) ? ncy : 0;
+            const T* row = G + ((int64_t)kz * ncy + ky) * ncx;
+            T accx = T(0);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                int kx = sx + a;
+                kx -= (kx >= ncx) ? ncx : 0;
+                accx += wx[a] * row[kx];
+            }
+            accy += wy[b] * accx;
+        }
+        acc += wz[c] * accy;
+    }
+    return acc;
+}
+
+// 2D Hermite of a coarse face plane P[row][col] (row stride `stride`).
+template <typename T>
+__device__ __forceinline__ T hermite2(const T* __restrict__ P, int64_t row_stride, int64_t col_stride, int nr,
+                                      int ncol, int sr, const T* wr, int sc, const T* wc) {
+    T acc = T(0);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        int kr = sr + b;
+        kr -= (kr >= nr) ? nr : 0;
+        T accc = T(0);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            int kc = sc + a;
+            kc -= (kc >= ncol) ? ncol : 0;
+            accc += wc[a] * P[kr * row_stride + kc * col_stride];
+        }
+        acc += wr[b] * accc;
+    }
+    return acc;
+}
+
+struct MrArgs {
+    int nx, ny, nz;       // fine cells
+    int nfx, nfy, nfz;    // fine face planes
+    int ncx, ncy, ncz;    // coarse cells
+    int ncfx, ncfy, ncfz; // coarse face planes
+    int wall[3];
+    double h;
+};
+
+template <typename T>
+__device__ __forceinline__ void load_w(const T* __restrict__ w, int i, T* out) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) out[m] = w[4 * i + m];
+}
+
+// Step (3) along x: one warp per fine x-line (j, k).  u(face i) = u_ref(j, k)
+// + h sum_{i' < i} Gx(i', j, k), the running sum kept in FP64 (warp scan).
+template <typename T>
+__global__ void mr_integrate_x(const T* __restrict__ gx, const T* __restrict__ uc, Tab<T> tx, Tab<T> ty, Tab<T> tz,
+                               MrArgs a, T* __restrict__ u) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= a.ny * a.nz) return;
+    const int j = warp % a.ny, k = warp / a.ny;
+    T wy[4], wz[4];
+    load_w(ty.w, j, wy);
+    load_w(tz.w, k, wz);
+    const int sy = ty.s[j], sz = tz.s[k];
+    T uref = T(0);
+    if (!a.wall[0]) {
+        // coarse x-face plane 0: uc[kz][ky][0]
+        uref = hermite2(uc, (int64_t)a.ncy * a.ncfx, (int64_t)a.ncfx, a.ncz, a.ncy, sz, wz, sy, wy);
+    }
+    T* row = u + ((int64_t)k * a.ny + j) * a.nfx;
+    double carry = 0.0;
+    for (int i0 = 0; i0 < a.nx; i0 += 32) {
+        const int i = i0 + lane;
+        double g = 0.0;
+        if (i < a.nx) {
+            T wx[4];
+            load_w(tx.w, i, wx);
+            g = (double)hermite3(gx, a.ncx, a.ncy, a.ncz, tx.s[i], wx, sy, wy, sz, wz);
+        }
+        // exclusive prefix sum within the warp
+        double incl = g;
+        for (int o = 1; o < 32; o <<= 1) {
+            const double t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const double excl = carry + incl - g;
+        if (i < a.nx) row[i] = uref + T(a.h * excl);
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (a.wall[0] && lane == 0) row[a.nx] = uref + T(a.h * carry);
+}
+
+// Step (3) along y: one thread per fine (i, k), marching j.
+template <typename T>
+__global__ void mr_integrate_y(const T* __restrict__ gy, const T* __restrict__ vc, Tab<T> tx, Tab<T> ty, Tab<T> tz,
+                               MrArgs a, T* __restrict__ v) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)a.nx * a.nz) return;
+    const int i = (int)(t % a.nx), k = (int)(t / a.nx);
+    T wx[4], wz[4];
+    load_w(tx.w, i, wx);
+    load_w(tz.w, k, wz);
+    const int sx = tx.s[i], sz = tz.s[k];
+    T vref = T(0);
+    if (!a.wall[1]) {
+        // coarse y-face plane 0: vc[kz][0][kx]
+        vref = hermite2(vc, (int64_t)a.ncfy * a.ncx, (int64_t)1, a.ncz, a.ncx, sz, wz, sx, wx);
+    }
+    double run = 0.0;
+    for (int j = 0; j < a.ny; ++j) {
+        T wy[4];
+        load_w(ty.w, j, wy);
+        const double g = (double)hermite3(gy, a.ncx, a.ncy, a.ncz, sx, wx, ty.s[j], wy, sz, wz);
+        v[((int64_t)k * a.nfy + j) * a.nx + i] = vref + T(a.h * run);
+        run += g;
+    }
+    if (a.wall[1]) v[((int64_t)k * a.nfy + a.ny) * a.nx + i] = vref + T(a.h * run);
+}
+
+// Step (3) along z: one thread per fine (i, j), marching k.  With walls the
+// reference plane is the bottom wall (w = 0).
+template <typename T>
+__global__ void mr_integrate_z(const T* __restrict__ gz, const T* __restrict__ wc, Tab<T> tx, Tab<T> ty, Tab<T> tz,
+                               MrArgs a, T* __restrict__ w) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)a.nx * a.ny) return;
+    const int i = (int)(t % a.nx), j = (int)(t / a.nx);
+    T wx[4], wy[4];
+    load_w(tx.w, i, wx);
+    load_w(ty.w, j, wy);
+    const int sx = tx.s[i], sy = ty.s[j];
+    T wref = T(0);
+    if (!a.wall[2]) {
+        // coarse z-face plane 0: wc[0][ky][kx]
+        wref = hermite2(wc, (int64_t)a.ncx, (int64_t)1, a.ncy, a.ncx, sy, wy, sx, wx);
+    }
+    double run = 0.0;
+    const int64_t plane = (int64_t)a.nx * a.ny;
+    for (int k = 0; k < a.nz; ++k) {
+        T wz[4];
+        load_w(tz.w, k, wz);
+        const double g = (double)hermite3(gz, a.ncx, a.ncy, a.ncz, sx, wx, sy, wy, tz.s[k], wz);
+        w[(int64_t)k * plane + t] = wref + T(a.h * run);
+        run += g;
+    }
+    if (a.wall[2]) w[(int64_t)a.nz * plane + t] = wref + T(a.h * run);
+}
+
+MrArgs mr_args(const ch_handle* h) {
+    MrArgs a;
+    a.nx = (int)h->n[0];
+    a.ny = (int)h->n[1];
+    a.nz = (int)h->n[2];
+    a.nfx = (int)h->nf[0];
+    a.nfy = (int)h->nf[1];
+    a.nfz = (int)h->nf[2];
+    a.ncx = (int)h->nc[0];
+    a.ncy = (int)h->nc[1];
+    a.ncz = (int)h->nc[2];
+    a.ncfx = (int)h->ncf[0];
+    a.ncfy = (int)h->ncf[1];
+    a.ncfz = (int)h->ncf[2];
+    for (int d = 0; d < 3; ++d) a.wall[d] = h->p.bc[d] == CH_NOFLUX;
+    a.h = h->p.h;
+    return a;
+}
+
+template <typename T>
+Tab<T> tab(const ch_handle* h, int d) {
+    Tab<T> t;
+    t.s = h->mr_start[d];
+    t.w = (const T*)(sizeof(T) == 8 ? (const void*)h->mr_w[d] : (const void*)(h->mr_w[d] + 4 * h->n[d]));
+    return t;
+}
+
+template <typename T>
+int interp(ch_handle* h) {
+    const MrArgs a = mr_args(h);
+    const double* xf = h->mr_coords;
+    const double* yf = xf + h->nc[0] + 1;
+    const double* zf = yf + h->nc[1] + 1;
+    const int64_t ncell = h->nc[0] * h->nc[1] * h->nc[2];
+    const int gblocks = (int)std::min<int64_t>((ncell + kThreads - 1) / kThreads, 8 * 152);
+    mr_gradients_kernel<T><<<gblocks, kThreads, 0, h->stream>>>(
+        (const T*)h->vel_c[0], (const T*)h->vel_c[1], (const T*)h->vel_c[2], xf, yf, zf, a.ncx, a.ncy, a.ncz, a.ncfx,
+        a.ncfy, !a.wall[0], !a.wall[1], !a.wall[2], (T*)h->grad_c[0], (T*)h->grad_c[1], (T*)h->grad_c[2]);
+    CHG_CUDA(h, cudaGetLastError());
+    const Tab<T> tx = tab<T>(h, 0), ty = tab<T>(h, 1), tz = tab<T>(h, 2);
+    {
+        const int64_t warps = (int64_t)a.ny * a.nz;
+        const unsigned blocks = (unsigned)((warps * 32 + kThreads - 1) / kThreads);
+        mr_integrate_x<T><<<blocks, kThreads, 0, h->stream>>>((const T*)h->grad_c[0], (const T*)h->vel_c[0], tx, ty,
+                                                              tz, a, (T*)h->vel[0]);
+        CHG_CUDA(h, cudaGetLastError());
+    }
+    {
+        const int64_t thr = (int64_t)a.nx * a.nz;
+        mr_integrate_y<T><<<(unsigned)((thr + kThreads - 1) / kThreads), kThreads, 0, h->stream>>>(
+            (const T*)h->grad_c[1], (const T*)h->vel_c[1], tx, ty, tz, a, (T*)h->vel[1]);
+        CHG_CUDA(h, cudaGetLastError());
+    }
+    {
+        const int64_t thr = (int64_t)a.nx * a.ny;
+        mr_integrate_z<T><<<(unsigned)((thr + kThreads - 1) / kThreads), kThreads, 0, h->stream>>>(
+            (const T*)h->grad_c[2], (const T*)h->vel_c[2], tx, ty, tz, a, (T*)h->vel[2]);
+        CHG_CUDA(h, cudaGetLastError());
+    }
+    return CH_OK;
+}
+
+}  // namespace
+
+namespace chg {
+
+void mr_destroy(ch_handle* h) {
+    cudaFree(h->mr_coords);
+    for (int d = 0; d < 3; ++d) {
+        cudaFree(h->mr_start[d]);
+        cudaFree(h->mr_w[d]);
+    }
+}
+
+// Called from ch_create with the caller's host face coordinates.
+int mr_build_tables(ch_handle* h, const double* xf, const double* yf, const double* zf) {
+    const int64_t ncoord = h->nc[0] + h->nc[1] + h->nc[2] + 3;
+    std::vector<double> all;
+    all.reserve(ncoord);
+    all.insert(all.end(), xf, xf + h->nc[0] + 1);
+    all.insert(all.end(), yf, yf + h->nc[1] + 1);
+    all.insert(all.end(), zf, zf + h->nc[2] + 1);
+    if (cudaMalloc(&h->mr_coords, ncoord * sizeof(double)) != cudaSuccess) return CH_ENOMEM;
+    CHG_CUDA(h, cudaMemcpy(h->mr_coords, all.data(), ncoord * sizeof(double), cudaMemcpyHostToDevice));
+    const double* dev_faces[3] = {h->mr_coords, h->mr_coords + h->nc[0] + 1,
+                                  h->mr_coords + h->nc[0] + h->nc[1] + 2};
+    for (int d = 0; d < 3; ++d) {
+        const int64_t n = h->n[d];
+        if (cudaMalloc(&h->mr_start[d], n * sizeof(int32_t)) != cudaSuccess) return CH_ENOMEM;
+        // doubles [n][4] followed by floats [n][4]
+        if (cudaMalloc(&h->mr_w[d], n * 4 * sizeof(double) + n * 4 * sizeof(float)) != cudaSuccess) return CH_ENOMEM;
+        mr_tables_kernel<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, h->stream>>>(
+            dev_faces[d], (int)h->nc[d], h->p.bc[d] == CH_PERIODIC, (int)n, h->p.h, h->mr_start[d], h->mr_w[d],
+            (float*)(h->mr_w[d] + 4 * n));
+        CHG_CUDA(h, cudaGetLastError());
+    }
+    CHG_CUDA(h, cudaStreamSynchronize(h->stream));
+    return CH_OK;
+}
+
+}  // namespace chg
+
+extern "C" {
+
+int ch_set_velocity_coarse(ch_handle* h, const void* uc, const void* vc, const void* wc) {
+    if (!h) return CH_EINVAL;
+    if (!h->nc[0]) return fail(h, CH_EINVAL, "ch_set_velocity_coarse: no coarse mesh at create");
+    if (!uc || !vc || !wc) return fail(h, CH_EINVAL, "ch_set_velocity_coarse: NULL pointer");
+    const void* src[3] = {uc, vc, wc};
+    for (int d = 0; d < 3; ++d) {
+        int64_t cnt = h->ncf[d];
+        for (int e = 0; e < 3; ++e)
+            if (e != d) cnt *= h->nc[e];
+        CHG_CUDA(h, cudaMemcpyAsync(h->vel_c[d], src[d], (size_t)cnt * h->esz, cudaMemcpyDeviceToDevice, h->stream));
+    }
+    return CH_OK;
+}
+
+int ch_interp_to_fine(ch_handle* h) {
+    if (!h) return CH_EINVAL;
+    if (!h->nc[0]) return fail(h, CH_EINVAL, "ch_interp_to_fine: no coarse mesh at create");
+    return h->prec == CH_F64 ? interp<double>(h) : interp<float>(h);
+}
+
+int ch_get_interp_tables(ch_handle* h, int dir, int32_t* start, double* weights) {
+    if (!h) return CH_EINVAL;
+    if (!h->nc[0]) return fail(h, CH_EINVAL, "ch_get_interp_tables: no coarse mesh at create");
+    if (dir < 0 || dir > 2 || !start || !weights) return fail(h, CH_EINVAL, "ch_get_interp_tables: bad argument");
+    const int64_t n = h->n[dir];
+    CHG_CUDA(h, cudaMemcpyAsync(start, h->mr_start[dir], n * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+    CHG_CUDA(h, cudaMemcpyAsync(weights, h->mr_w[dir], n * 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CHG_CUDA(h, cudaStreamSynchronize(h->stream));
+    return CH_OK;
+}
+
+}  // extern "C"

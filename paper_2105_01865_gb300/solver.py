@@ -1,0 +1,112 @@
+"""Python-side owner of one Cahn-Hilliard solver handle.
+
+Holds the torch tensors the C ABI borrows (C and the workspace) and the
+stream; every operation is one call into libch.so through ``capi``.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import capi
+
+
+class Solver:
+    """Fine-mesh Cahn-Hilliard solver on one GPU.
+
+    shape = (nz, ny, nx); bc = (bc_x, bc_y, bc_z) with capi.CH_PERIODIC /
+    capi.CH_NOFLUX; precision "f32" or "f64".  C0 is a numpy or torch array of
+    the initial volume fraction.  coarse_faces = (xf, yf, zf) enables the
+    velocity transfer from a stretched coarse mesh.
+    """
+
+    def __init__(self, shape, h, bc, cn, pe, dt, C0, precision="f32", w=4.0, weno_eps=1e-6,
+                 advect=False, coarse_faces=None, device="cuda:0", stream=None):
+        self.shape = tuple(int(s) for s in shape)
+        self.bc = tuple(bc)
+        self.dtype = torch.float64 if precision == "f64" else torch.float32
+        self.device = torch.device(device)
+        # a dedicated stream by default, so ch_step runs as a captured CUDA graph
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        prec = capi.CH_F64 if precision == "f64" else capi.CH_F32
+        self.params = capi.make_params(self.shape, h, bc, cn, pe, dt, prec, w, weno_eps,
+                                       advect or coarse_faces is not None, coarse_faces)
+        nbytes = capi.ch_workspace_bytes(self.params)
+        if nbytes == 0:
+            raise capi.CHError(capi.CH_EINVAL, "invalid parameters")
+        self.C = torch.as_tensor(np.asarray(C0) if not torch.is_tensor(C0) else C0).to(
+            device=self.device, dtype=self.dtype).contiguous().clone()
+        self.work = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self._order()
+        with torch.cuda.device(self.device):
+            self.handle = capi.ch_create(self.params, self.C, self.work, self.stream)
+        nz, ny, nx = self.shape
+        nf = [n + (1 if b == capi.CH_NOFLUX else 0) for n, b in zip((nx, ny, nz), self.bc)]
+        self.vel_shapes = ((nz, ny, nf[0]), (nz, nf[1], nx), (nf[2], ny, nx))
+        if coarse_faces is not None:
+            nc = [len(f) - 1 for f in coarse_faces]
+            ncf = [n + (1 if b == capi.CH_NOFLUX else 0) for n, b in zip(nc, self.bc)]
+            self.coarse_shapes = ((nc[2], nc[1], ncf[0]), (nc[2], ncf[1], nc[0]), (ncf[2], nc[1], nc[0]))
+
+    def _order(self):
+        """Make the library's stream wait for tensors prepared on torch's current stream."""
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+
+    def _dev(self, a):
+        t = a if torch.is_tensor(a) else torch.as_tensor(np.asarray(a))
+        return t.to(device=self.device, dtype=self.dtype).contiguous()
+
+    def set_velocity_fine(self, u, v, w):
+        self._vel_keep = [self._dev(a) for a in (u, v, w)]
+        self._order()
+        capi.ch_set_velocity_fine(self.handle, *self._vel_keep)
+
+    def set_velocity_coarse(self, uc, vc, wc):
+        self._velc_keep = [self._dev(a) for a in (uc, vc, wc)]
+        self._order()
+        capi.ch_set_velocity_coarse(self.handle, *self._velc_keep)
+
+    def interp_to_fine(self):
+        capi.ch_interp_to_fine(self.handle)
+
+    def velocity_fine(self):
+        out = [torch.empty(s, dtype=self.dtype, device=self.device) for s in self.vel_shapes]
+        self._order()
+        capi.ch_get_velocity_fine(self.handle, *out)
+        self.stream.synchronize()
+        return out
+
+    def interp_tables(self, direction):
+        n = (self.shape[2], self.shape[1], self.shape[0])[direction]
+        return capi.ch_get_interp_tables(self.handle, direction, n)
+
+    def step(self, nsteps=1):
+        capi.ch_step(self.handle, nsteps)
+
+    def mass(self):
+        return capi.ch_mass(self.handle)
+
+    def free_energy(self):
+        return capi.ch_free_energy(self.handle)
+
+    def sync(self):
+        capi.ch_sync(self.handle)
+
+    def field(self):
+        self.stream.synchronize()
+        return self.C.detach().cpu().numpy().astype(np.float64)
+
+    def launches_per_step(self):
+        return capi.ch_launches_per_step(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            self.stream.synchronize()
+            capi.ch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

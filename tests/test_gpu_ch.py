@@ -1,0 +1,218 @@
+"""GPU parity of the Cahn-Hilliard step (libch.so through the C ABI) against
+the CPU FP64 oracle on the same seeded inputs.
+
+Bars: FP64 mode <= 1e-12 relative L2 on C; FP32 mode <= 1e-5 relative L2 on
+C after 100 steps of the periodic single-drop box; mass conserved to rounding.
+"""
+import numpy as np
+import pytest
+
+from oracle import ch_oracle as co
+from paper_2105_01865_gb300 import inputs, stability
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2105_01865_gb300 import build, capi
+    build.build()
+    capi.load()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def make(shape, h, bc, cn, pe, dt, C0, prec, vel=None, w=4.0):
+    from paper_2105_01865_gb300.solver import Solver
+    s = Solver(shape, h, bc, cn, pe, dt, C0, precision=prec, w=w, advect=vel is not None)
+    if vel is not None:
+        s.set_velocity_fine(*vel)
+    return s
+
+
+def oracle_params(shape, h, bc, cn, pe, dt, w=4.0):
+    nz, ny, nx = shape
+    return co.Params(nx, ny, nz, h, cn=cn, pe=pe, dt=dt, bc=bc, w=w)
+
+
+def curl_vel(shape, h, bc, seed, kmax=3):
+    nz, ny, nx = shape
+    return inputs.curl_velocity(inputs.uniform_faces(nx, nx * h), inputs.uniform_faces(ny, ny * h),
+                                inputs.uniform_faces(nz, nz * h), bc, seed, kmax=kmax)
+
+
+# ---------------------------------------------------------------------------
+# FP64 (the plain method) at 1e-12
+# ---------------------------------------------------------------------------
+
+def test_fp64_single_drop_box_100_steps():
+    f = inputs.single_drop_box(64)
+    dt = 0.9 * stability.stable_dt(f["shape"], f["h"], f["bc"], f["cn"], f["pe"])
+    s = make(f["shape"], f["h"], f["bc"], f["cn"], f["pe"], dt, f["C"], "f64")
+    s.step(100)
+    got = s.field()
+    ref = co.step(f["C"], None, oracle_params(f["shape"], f["h"], f["bc"], f["cn"], f["pe"], dt), 100)
+    assert rel_l2(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("shape,bc", [
+    ((9, 17, 33), (co.NOFLUX, co.PERIODIC, co.NOFLUX)),      # ragged x/y tiles, one z chunk
+    ((37, 11, 40), (co.PERIODIC, co.NOFLUX, co.PERIODIC)),   # several z chunks, ragged tail
+    ((6, 5, 7), (co.PERIODIC, co.PERIODIC, co.PERIODIC)),    # near the minimum size
+    ((5, 6, 5), (co.NOFLUX, co.NOFLUX, co.NOFLUX)),          # minimum size, all walls
+])
+def test_fp64_advected_ragged(shape, bc):
+    h = 1.0 / 16
+    cn = 0.75 * h
+    pe = 0.9 / cn
+    nz, ny, nx = shape
+    rng = np.random.default_rng(11)
+    centres, radii = inputs.random_drops(rng, 3, (nx * h, ny * h, nz * h), 0.05, 0.15, 2 * cn,
+                                         tuple(b == co.NOFLUX for b in bc))
+    C0 = inputs.drops_field(shape, h, bc, centres, radii, cn)
+    C0 = C0 + 0.05 * rng.standard_normal(shape)
+    vel = curl_vel(shape, h, bc, 5)
+    dt = 0.4 * h
+    s = make(shape, h, bc, cn, pe, dt, C0, "f64", vel)
+    s.step(6)
+    got = s.field()
+    ref = co.step(C0, vel, oracle_params(shape, h, bc, cn, pe, dt), 6)
+    assert rel_l2(got, ref) <= 1e-12
+
+
+def test_fp64_w3_variant_and_large_c():
+    """The derived w = 3 operator (reading R1) with a large implicit coefficient."""
+    shape, h = (20, 24, 36), 1.0 / 24
+    bc = (co.PERIODIC, co.PERIODIC, co.NOFLUX)
+    cn = 0.75 * h
+    C0 = inputs.drops_field(shape, h, bc, [(0.7, 0.5, 0.4)], [0.25], cn)
+    s = make(shape, h, bc, cn, 10.0, 0.05, C0, "f64", w=3.0)
+    s.step(4)
+    ref = co.step(C0, None, oracle_params(shape, h, bc, cn, 10.0, 0.05, w=3.0), 4)
+    assert rel_l2(s.field(), ref) <= 1e-12
+
+
+def test_fp64_mass_and_energy_reductions():
+    shape, h = (20, 18, 40), 1.0 / 20
+    bc = (co.PERIODIC, co.NOFLUX, co.NOFLUX)
+    cn = 0.75 * h
+    rng = np.random.default_rng(2)
+    C0 = 0.5 + 0.3 * rng.standard_normal(shape)
+    s = make(shape, h, bc, cn, 100.0, 1e-3, C0, "f64")
+    p = oracle_params(shape, h, bc, cn, 100.0, 1e-3)
+    assert abs(s.mass() - co.mass(C0, p)) <= 1e-12 * abs(co.mass(C0, p))
+    assert abs(s.free_energy() - co.free_energy(C0, p)) <= 1e-12 * abs(co.free_energy(C0, p))
+
+
+def test_fp64_mass_conserved_with_flow():
+    shape, h = (32, 24, 40), 1.0 / 32
+    bc = (co.PERIODIC, co.PERIODIC, co.NOFLUX)
+    cn = 0.75 * h
+    C0 = inputs.drops_field(shape, h, bc, [(0.6, 0.4, 0.5)], [0.2], cn)
+    vel = curl_vel(shape, h, bc, 9)
+    s = make(shape, h, bc, cn, 0.9 / cn, 0.4 * h, C0, "f64", vel)
+    m0 = s.mass()
+    s.step(50)
+    assert abs(s.mass() - m0) <= 1e-13 * abs(m0)
+
+
+# ---------------------------------------------------------------------------
+# FP32 precision form
+# ---------------------------------------------------------------------------
+
+def test_fp32_single_drop_box_100_steps():
+    f = inputs.single_drop_box(64)
+    dt = 0.9 * stability.stable_dt(f["shape"], f["h"], f["bc"], f["cn"], f["pe"])
+    ref = co.step(f["C"], None, oracle_params(f["shape"], f["h"], f["bc"], f["cn"], f["pe"], dt), 100)
+    s = make(f["shape"], f["h"], f["bc"], f["cn"], f["pe"], dt, f["C"], "f32")
+    m0 = s.mass()
+    s.step(100)
+    err = rel_l2(s.field(), ref)
+    print(f"FP32 single-drop 64^3, 100 steps: rel L2 on C = {err:.3e}")
+    assert err <= 1e-5
+    assert abs(s.mass() - m0) <= 1e-6 * abs(m0)
+
+
+def test_fp32_shear_drop_small():
+    f = inputs.shear_drop_box(64, 64, 32)
+    h = f["h"]
+    dt = min(0.9 * stability.stable_dt(f["shape"], h, f["bc"], f["cn"], f["pe"]), 0.5 * h / 0.5)
+    ref = co.step(f["C"], f["vel"], oracle_params(f["shape"], h, f["bc"], f["cn"], f["pe"], dt), 20)
+    s = make(f["shape"], h, f["bc"], f["cn"], f["pe"], dt, f["C"], "f32", f["vel"])
+    s.step(20)
+    err = rel_l2(s.field(), ref)
+    print(f"FP32 shear drop 64x64x32, 20 steps: rel L2 on C = {err:.3e}")
+    assert err <= 1e-5
+
+
+def test_full_size_shear_drop_one_step_and_mass():
+    """256 x 256 x 128 drop in shear in the launch configuration the bench
+    times: one step against the oracle, then mass over 20 more steps."""
+    f = inputs.shear_drop_box(256, 256, 128)
+    h = f["h"]
+    dt = min(0.9 * stability.stable_dt(f["shape"], h, f["bc"], f["cn"], f["pe"]), 0.5 * h / 0.5)
+    s = make(f["shape"], h, f["bc"], f["cn"], f["pe"], dt, f["C"], "f32", f["vel"])
+    s.step(1)
+    ref = co.step(f["C"], f["vel"], oracle_params(f["shape"], h, f["bc"], f["cn"], f["pe"], dt), 1)
+    err = rel_l2(s.field(), ref)
+    print(f"FP32 shear drop 256x256x128, 1 step: rel L2 on C = {err:.3e}")
+    assert err <= 1e-6
+    m0 = s.mass()
+    s.step(20)
+    assert abs(s.mass() - m0) <= 1e-6 * abs(m0)
+
+
+# ---------------------------------------------------------------------------
+# Edge cases and error paths (host-made failures only)
+# ---------------------------------------------------------------------------
+
+def test_zero_steps_is_a_no_op():
+    f = inputs.single_drop_box(16)
+    s = make(f["shape"], f["h"], f["bc"], f["cn"], f["pe"], 1e-3, f["C"], "f64")
+    s.step(0)
+    assert np.array_equal(s.field(), f["C"])
+
+
+def test_invalid_arguments_raise():
+    from paper_2105_01865_gb300 import capi
+    with pytest.raises(capi.CHError):
+        make((4, 8, 8), 0.1, (0, 0, 0), 0.1, 1.0, 1e-3, np.zeros((4, 8, 8)), "f32")
+    f = inputs.single_drop_box(16)
+    s = make(f["shape"], f["h"], f["bc"], f["cn"], f["pe"], 1e-3, f["C"], "f32")
+    with pytest.raises(capi.CHError):
+        s.step(-1)
+    with pytest.raises(capi.CHError):
+        s.set_velocity_fine(*[np.zeros(x) for x in s.vel_shapes])      # created without advection
+
+
+def test_nonfinite_input_is_reported():
+    from paper_2105_01865_gb300 import capi
+    f = inputs.single_drop_box(16)
+    C0 = f["C"].copy()
+    C0[3, 4, 5] = np.nan
+    s = make(f["shape"], f["h"], f["bc"], f["cn"], f["pe"], 1e-3, C0, "f32")
+    s.step(1)
+    with pytest.raises(capi.CHError) as e:
+        s.sync()
+    assert e.value.status == capi.CH_ENONFINITE
+    s.sync()          # the flag was cleared
+
+
+def test_graph_replay_matches_direct_launches():
+    """ch_step on a user stream replays a captured graph; on the legacy
+    stream it launches directly.  Both give bit-identical fields."""
+    from paper_2105_01865_gb300.solver import Solver
+    f = inputs.shear_drop_box(40, 36, 20)
+    args = (f["shape"], f["h"], f["bc"], f["cn"], f["pe"], 0.3 * f["h"], f["C"])
+    a = Solver(*args, precision="f32", advect=True)
+    b = Solver(*args, precision="f32", advect=True, stream=torch.cuda.default_stream())
+    for s in (a, b):
+        s.set_velocity_fine(*f["vel"])
+        s.step(5)
+    assert np.array_equal(a.field(), b.field())

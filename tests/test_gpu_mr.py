@@ -1,0 +1,108 @@
+"""GPU parity of the multiple-resolution velocity transfer (Sec. 3.4) against
+the oracle: index maps bit-exact, weights and fine velocities in FP64 to
+1e-12, FP32 within its rounding, and the divergence identity at full size."""
+import numpy as np
+import pytest
+
+from oracle import mr_oracle as mo
+from paper_2105_01865_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+PER, WALL = 0, 1
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2105_01865_gb300 import build, capi
+    build.build()
+    capi.load()
+
+
+def coarse_case(nc, box, bc, seed, stretch=2.0, kmax=4):
+    ncx, ncy, ncz = nc
+    xf = inputs.uniform_faces(ncx, box[0])
+    yf = inputs.uniform_faces(ncy, box[1])
+    zf = inputs.stretched_faces(ncz, box[2], stretch) if bc[2] == WALL else inputs.uniform_faces(ncz, box[2])
+    uc, vc, wc = inputs.curl_velocity(xf, yf, zf, bc, seed, kmax=kmax)
+    return (xf, yf, zf), (uc, vc, wc)
+
+
+def solver(fine_n, h, bc, faces, prec):
+    from paper_2105_01865_gb300.solver import Solver
+    nx, ny, nz = fine_n
+    return Solver((nz, ny, nx), h, bc, 0.75 * h, 100.0, 1e-3, np.zeros((nz, ny, nx)), precision=prec,
+                  coarse_faces=faces)
+
+
+@pytest.mark.parametrize("bc", [(PER, PER, WALL), (PER, PER, PER), (WALL, PER, WALL)])
+def test_tables_bit_exact_indices(bc):
+    fine_n, h = (48, 40, 24), 1.0 / 24
+    faces, _ = coarse_case((12, 10, 9), (2.0, 40 / 24, 1.0), bc, 1)
+    s = solver(fine_n, h, bc, faces, "f64")
+    ref = mo.tables(*faces, fine_n, h, bc)
+    for d in range(3):
+        start, w = s.interp_tables(d)
+        assert np.array_equal(start, ref[d][0]), d
+        np.testing.assert_allclose(w, ref[d][1], rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 2e-6)])
+@pytest.mark.parametrize("bc", [(PER, PER, WALL), (PER, PER, PER)])
+def test_fine_velocity_matches_oracle(prec, tol, bc):
+    fine_n, h = (40, 36, 20), 1.0 / 20
+    box = (2.0, 36 / 20, 1.0)
+    faces, (uc, vc, wc) = coarse_case((10, 9, 7), box, bc, 3)
+    s = solver(fine_n, h, bc, faces, prec)
+    s.set_velocity_coarse(uc, vc, wc)
+    s.interp_to_fine()
+    got = [t.cpu().numpy().astype(np.float64) for t in s.velocity_fine()]
+    (u, v, w), _ = mo.transfer(uc, vc, wc, *faces, fine_n, h, bc)
+    scale = max(np.abs(a).max() for a in (u, v, w))
+    for g, r in zip(got, (u, v, w)):
+        assert g.shape == r.shape
+        assert np.abs(g - r).max() <= tol * scale
+
+
+def test_full_size_transfer_sampled_lines_and_divergence():
+    """Coarse 256 x 256 x 128 (tanh-stretched z) to fine 1024 x 1024 x 512 in
+    FP32: sampled fine lines against the oracle, and the discrete divergence
+    of the fine field away from the periodic wrap planes."""
+    bc = (PER, PER, WALL)
+    fine_n, h = (1024, 1024, 512), 1.0 / 512
+    faces, (uc, vc, wc) = coarse_case((256, 256, 128), (2.0, 2.0, 1.0), bc, 3, kmax=8)
+    s = solver(fine_n, h, bc, faces, "f32")
+    s.set_velocity_coarse(uc, vc, wc)
+    s.interp_to_fine()
+    u, v, w = s.velocity_fine()
+    scale = float(max(u.abs().max(), v.abs().max(), w.abs().max()))
+    # divergence on the device (torch arithmetic on the library's output)
+    nx, ny, nz = fine_n
+    du = u[:, :, 1:] - u[:, :, :-1]                         # cells 0..nx-2
+    dv = v[:, 1:, :] - v[:, :-1, :]
+    dw = w[1:] - w[:-1]
+    div = (du[:, :-1, :] + dv[:, :, :-1] + dw[:, :-1, :-1]) / h
+    assert float(div.abs().max()) * h <= 1e-5 * scale
+    # sampled lines against the oracle's 64-point stencil
+    tabs = mo.tables(*faces, fine_n, h, bc)
+    gx, gy, gz = mo.coarse_gradients(uc, vc, wc, *faces, bc)
+    rng = np.random.default_rng(0)
+    for _ in range(3):
+        j, k = int(rng.integers(ny)), int(rng.integers(nz))
+        sub = [tabs[0], (tabs[1][0][[j]], tabs[1][1][[j]]), (tabs[2][0][[k]], tabs[2][1][[k]])]
+        G = mo.interp_3d(gx, sub)[0, 0]
+        uref = mo.interp_plane(uc[:, :, 0], sub[2], sub[1])[0, 0]
+        line = uref + np.concatenate([[0.0], np.cumsum(G)[:-1] * h])
+        got = u[k, j].cpu().numpy().astype(np.float64)
+        assert np.abs(got - line).max() <= 2e-6 * scale
+    for _ in range(2):
+        i, j = int(rng.integers(nx)), int(rng.integers(ny))
+        sub = [(tabs[0][0][[i]], tabs[0][1][[i]]), (tabs[1][0][[j]], tabs[1][1][[j]]), tabs[2]]
+        G = mo.interp_3d(gz, sub)[:, 0, 0]
+        line = np.concatenate([[0.0], np.cumsum(G) * h])
+        got = w[:, j, i].cpu().numpy().astype(np.float64)
+        assert np.abs(got - line).max() <= 2e-6 * scale
