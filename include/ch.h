@@ -162,6 +162,23 @@ int ch_launches_per_step(const ch_handle* h);
  * Errors: CH_EINVAL, CH_ECUDA. */
 int ch_profile_step(ch_handle* h, int64_t nsteps, double* ms_out);
 
+/* Mass h^3 * sum(C) without any device allocation; the paper has no
+ * counterpart (it is an interface for callers that cannot call cudaMalloc,
+ * e.g. an application that owns the device memory budget through its own
+ * pool, or a plug-in handed only pointers).  C: device array of nx*ny*nz
+ * values, float (CH_F32) or double (CH_F64).  out: DEVICE pointer to one
+ * double, written asynchronously on `stream` (a cudaStream_t, NULL = legacy
+ * stream).  Scratch: a fixed 512 KB file-scope device array of 65536 FP64
+ * partial sums of 4096 cells each, so at most 268435456 cells; larger grids
+ * return CH_EINVAL with a message on stderr.  The array is held by every GPU
+ * that loads the library until exit and is shared by all calls: calls that
+ * overlap on the GPU race.  Every partial a call reads is written by that
+ * call first, so nothing needs clearing.  The first call on a device looks up
+ * the array's address with that device current; make it before any stream
+ * capture.  Errors: CH_EINVAL, CH_ECUDA. */
+int ch_mass_noalloc(const void* C, int64_t nx, int64_t ny, int64_t nz, double h, int precision, double* out,
+                    void* stream);
+
 /* Static description of a status code. */
 const char* ch_error_string(int status);
 

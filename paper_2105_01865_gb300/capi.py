@@ -62,6 +62,8 @@ SIGNATURES = [
     ("ch_sync", ctypes.c_int, [_P]),
     ("ch_launches_per_step", ctypes.c_int, [_P]),
     ("ch_profile_step", ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]),
+    ("ch_mass_noalloc", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                                        ctypes.c_int, _P, _P]),
     ("ch_error_string", ctypes.c_char_p, [ctypes.c_int]),
     ("ch_last_error", ctypes.c_char_p, [_P]),
 ]
@@ -187,6 +189,16 @@ def ch_profile_step(handle, nsteps):
     out = (ctypes.c_double * 4)()
     _check(load().ch_profile_step(handle, nsteps, out), handle, "ch_profile_step")
     return list(out)
+
+
+def ch_mass_noalloc(C, h, out, stream):
+    """h^3 sum(C) into the one-element FP64 device tensor ``out`` on ``stream``,
+    with no device allocation by the library (scratch is a fixed device array)."""
+    nz, ny, nx = C.shape
+    prec = CH_F64 if C.element_size() == 8 else CH_F32
+    st = load().ch_mass_noalloc(_ptr(C), nx, ny, nz, h, prec, _ptr(out), ctypes.c_void_p(stream.cuda_stream))
+    if st != CH_OK:
+        raise CHError(st, f"ch_mass_noalloc: {ch_error_string(st)} (grid limit 268435456 cells)")
 
 
 def ch_error_string(status):
