@@ -19,18 +19,12 @@ constexpr int kRK = 3;  // RK3 substeps (Sec. 3)
 constexpr double kGamma[kRK] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
 constexpr double kRho[kRK] = {0.0, -17.0 / 60.0, -5.0 / 12.0};
 
-// Coefficients of one factorised line operator (I + c A_d) of one direction
-// and substep, stored in the handle's precision (device memory).
-struct LineCoefs {
-    const void* l1;    // LU sub-diagonal multipliers (row j, col j-1)
-    const void* l2;    // LU multipliers (row j, col j-2)
-    const void* u1;    // U first super-diagonal
-    const void* u2;    // U second super-diagonal
-    const void* dinv;  // 1 / U diagonal
-    const void* W;     // periodic only: [n][4] Woodbury left vectors
-    const void* Z;     // periodic only: [n][4] Woodbury right vectors
-    const void* S;     // periodic only: [4][4] capacitance inverse
-    int n;
+// Warp-scan tables of one factorised line operator (I + c A_d) of one
+// direction and substep, in the handle's precision (device memory).
+struct LineTables {
+    const void* base;  // block laid out by warp_layout(M)
+    int n;             // cells along the line
+    int M;             // rows per lane (32 M >= n)
     int periodic;
 };
 
@@ -55,7 +49,7 @@ struct ch_handle {
     int64_t ncf[3];     // coarse face planes
     // library-owned device memory
     void* coef_buf;
-    chg::LineCoefs coefs[3][chg::kRK];
+    chg::LineTables lines[3][chg::kRK];
     double* red_partials;
     double* red_out;
     unsigned int* status;

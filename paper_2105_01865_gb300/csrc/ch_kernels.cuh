@@ -24,22 +24,24 @@ constexpr int kTY = 8;    // explicit-kernel tile, y (warps per CTA)
 constexpr int kTZ = 16;   // z-planes marched per CTA
 constexpr int kHalo = 3;  // WENO5 needs three cells on each side
 
+template <typename T>
 struct RhsArgs {
     int nx, ny, nz;
     int bcx, bcy, bcz;
     int nfx, nfy, nfz;
-    double inv_h, inv_h2;
-    double mob;        // M = 1/Pe
-    double dtg;        // dt * gamma_l
-    double dtr;        // dt * rho_l
-    double impl;       // alpha_l dt M kappa (multiplies the raw [1,-4,6,-4,1] sums)
-    double eps;        // WENO regulariser
-    int has_prev;      // rho_l != 0
+    T inv_h, inv_h2;
+    T mob;        // M = 1/Pe
+    T dtg;        // dt * gamma_l
+    T dtr;        // dt * rho_l
+    T impl;       // alpha_l dt M kappa (multiplies the raw [1,-4,6,-4,1] sums)
+    T eps;        // WENO regulariser
+    int has_prev; // rho_l != 0
 };
 
 // Neighbour index with the boundary rule of Sec. 3.1: periodic wrap, or the
 // mirror about a wall face (ghost C_{-1-m} = C_m).  Clamped so that cells
-// outside the domain in a ragged tile still read valid memory.
+// outside the domain in a ragged tile still read valid memory.  Uses integer
+// division, so it is only called once per CTA to build index tables.
 __device__ __forceinline__ int bc_index(int i, int n, int bc) {
     if (bc == CH_PERIODIC) {
         i %= n;
@@ -51,56 +53,85 @@ __device__ __forceinline__ int bc_index(int i, int n, int bc) {
     return min(max(i, 0), n - 1);
 }
 
+// The same rule for indices at most one period outside [0, n) (n >= 5 and
+// offsets of at most 4), without division.
+__device__ __forceinline__ int bc_near(int i, int n, int bc) {
+    if (i < 0) return bc == CH_PERIODIC ? i + n : -1 - i;
+    if (i >= n) return bc == CH_PERIODIC ? i - n : 2 * n - 1 - i;
+    return i;
+}
+
 template <typename T>
 __device__ __forceinline__ T psi_p(T c) {  // psi'(C) = C^3 - 1.5 C^2 + 0.5 C (Eq. eq-ch)
     return c * (c * (c - T(1.5)) + T(0.5));
 }
 
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+
 // Fifth-order WENO (Jiang-Shu) value at the face between v3 and v4 from the
-// upwind-biased stencil v1..v5 (Sec. 3: "fifth-order WENO").
+// upwind-biased stencil v1..v5 (Sec. 3: "fifth-order WENO").  The nonlinear
+// weights alpha_k = d_k / (eps + beta_k)^2, normalised, are formed over a
+// common denominator so that one division serves all three.
 template <typename T>
 __device__ __forceinline__ T weno5(T v1, T v2, T v3, T v4, T v5, T eps) {
-    const T q0 = (T(2) * v1 - T(7) * v2 + T(11) * v3) * T(1.0 / 6.0);
-    const T q1 = (-v2 + T(5) * v3 + T(2) * v4) * T(1.0 / 6.0);
-    const T q2 = (T(2) * v3 + T(5) * v4 - v5) * T(1.0 / 6.0);
+    const T q0 = T(2) * v1 - T(7) * v2 + T(11) * v3;   // 6 x candidate values
+    const T q1 = -v2 + T(5) * v3 + T(2) * v4;
+    const T q2 = T(2) * v3 + T(5) * v4 - v5;
     const T d0 = v1 - T(2) * v2 + v3, e0 = v1 - T(4) * v2 + T(3) * v3;
     const T d1 = v2 - T(2) * v3 + v4, e1 = v2 - v4;
     const T d2 = v3 - T(2) * v4 + v5, e2 = T(3) * v3 - T(4) * v4 + v5;
-    const T b0 = T(13.0 / 12.0) * d0 * d0 + T(0.25) * e0 * e0;
-    const T b1 = T(13.0 / 12.0) * d1 * d1 + T(0.25) * e1 * e1;
-    const T b2 = T(13.0 / 12.0) * d2 * d2 + T(0.25) * e2 * e2;
-    const T s0 = eps + b0, s1 = eps + b1, s2 = eps + b2;
-    const T a0 = T(0.1) / (s0 * s0);
-    const T a1 = T(0.6) / (s1 * s1);
-    const T a2 = T(0.3) / (s2 * s2);
-    return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+    const T s0 = eps + (T(13.0 / 12.0) * d0 * d0 + T(0.25) * e0 * e0);
+    const T s1 = eps + (T(13.0 / 12.0) * d1 * d1 + T(0.25) * e1 * e1);
+    const T s2 = eps + (T(13.0 / 12.0) * d2 * d2 + T(0.25) * e2 * e2);
+    const T t0 = s0 * s0, t1 = s1 * s1, t2 = s2 * s2;
+    const T w0 = T(0.1) * (t1 * t2), w1 = T(0.6) * (t0 * t2), w2 = T(0.3) * (t0 * t1);
+    return fdiv(w0 * q0 + w1 * q1 + w2 * q2, T(6) * (w0 + w1 + w2));
 }
 
 // Flux u_f C_f through a face, C_f from the upwind WENO5 stencil.  m3..p2 are
 // the cells f-3 .. f+2 around the face f (between cells f-1 and f).
 template <typename T>
 __device__ __forceinline__ T face_flux(T vel, T m3, T m2, T m1, T p0, T p1, T p2, T eps) {
-    const T cf = vel >= T(0) ? weno5(m3, m2, m1, p0, p1, eps) : weno5(p2, p1, p0, m1, m2, eps);
-    return vel * cf;
+    const bool up = vel >= T(0);
+    const T a1 = up ? m3 : p2, a2 = up ? m2 : p1, a3 = up ? m1 : p0, a4 = up ? p0 : m1, a5 = up ? p1 : m2;
+    return vel * weno5(a1, a2, a3, a4, a5, eps);
+}
+
+// Asynchronous global -> shared copies (cp.async): one element, 4 or 8 bytes.
+__device__ __forceinline__ void cp_async_elem(float* smem, const float* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(double* smem, const double* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 // ---------------------------------------------------------------------------
 // Explicit right-hand side.  A CTA owns a 32 x 8 column of cells and marches
 // kTZ planes in z.  Each plane (with a 3-cell halo in x and y) is staged in
-// shared memory; the cell's own z-column lives in a 6-register queue.  Every
-// face flux is computed exactly once (lower faces by their cell, the extra
-// upper faces of the tile by dedicated lanes, z-faces carried between planes),
-// so the fluxes telescope bit-exactly and mass is conserved to rounding.
+// shared memory through per-CTA index tables (no division in the loop); the
+// cell's own z-column lives in a 6-register queue.  Every face flux is
+// computed exactly once (lower faces by their cell, the extra upper faces of
+// the tile by dedicated lanes, z-faces carried between planes), so the
+// fluxes telescope bit-exactly and mass is conserved to rounding.
 // ---------------------------------------------------------------------------
 template <typename T, bool ADV>
 __global__ void __launch_bounds__(kTX * kTY)
 ch_explicit_rhs(const T* __restrict__ C, const T* __restrict__ u, const T* __restrict__ v,
                 const T* __restrict__ w, const T* __restrict__ Hprev, T* __restrict__ Hout,
-                T* __restrict__ r, RhsArgs a) {
+                T* __restrict__ r, RhsArgs<T> a) {
     constexpr int PX = kTX + 2 * kHalo, PY = kTY + 2 * kHalo;
-    __shared__ T Cs[2][PY][PX];
+    __shared__ __align__(16) T Cs[3][PY][PX];
     __shared__ T Fx[ADV ? kTY : 1][kTX + 1];
     __shared__ T Fy[ADV ? kTY + 1 : 1][kTX];
+    __shared__ int gi_tab[PX], gj_tab[PY];
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kTX + tx;
     const int i0 = blockIdx.x * kTX, j0 = blockIdx.y * kTY, k0 = blockIdx.z * kTZ;
@@ -108,50 +139,75 @@ ch_explicit_rhs(const T* __restrict__ C, const T* __restrict__ u, const T* __res
     const bool in_xy = (i < a.nx) && (j < a.ny);
     const int ic = min(i, a.nx - 1), jc = min(j, a.ny - 1);
     const int64_t plane = (int64_t)a.nx * a.ny;
-    const T eps = T(a.eps);
+    const int64_t col = (int64_t)jc * a.nx + ic;
+    const T eps = a.eps;
     const int kend = min(k0 + kTZ, a.nz);
+
+    if (tid < PX) gi_tab[tid] = bc_index(i0 + tid - kHalo, a.nx, a.bcx);
+    else if (tid < PX + PY) gj_tab[tid - PX] = bc_index(j0 + (tid - PX) - kHalo, a.ny, a.bcy);
+
+    // face indices and wall flags of this thread's faces (fixed over the march)
+    const bool wall_x = (a.bcx == CH_NOFLUX) && (i <= 0 || i >= a.nx);
+    const int fi = (a.bcx == CH_PERIODIC) ? bc_index(i, a.nx, CH_PERIODIC) : min(i, a.nx);
+    const bool wall_y = (a.bcy == CH_NOFLUX) && (j <= 0 || j >= a.ny);
+    const int fj = (a.bcy == CH_PERIODIC) ? bc_index(j, a.ny, CH_PERIODIC) : min(j, a.ny);
+    // extra faces: x-face i0+32 of row (j0 + tx) for warp 0 lanes < 8, y-face j0+8 for warp 1
+    const int ie = i0 + kTX, je_row = min(j0 + tx, a.ny - 1);
+    const bool wall_xe = (a.bcx == CH_NOFLUX) && (ie >= a.nx);
+    const int fie = (a.bcx == CH_PERIODIC) ? bc_index(ie, a.nx, CH_PERIODIC) : min(ie, a.nx);
+    const int je = j0 + kTY;
+    const bool wall_ye = (a.bcy == CH_NOFLUX) && (je >= a.ny);
+    const int fje = (a.bcy == CH_PERIODIC) ? bc_index(je, a.ny, CH_PERIODIC) : min(je, a.ny);
 
     // z-column queue: q[m] = C(ic, jc, k - 2 + m), m = 0..5
     T q[6];
 #pragma unroll
-    for (int m = 0; m < 6; ++m)
-        q[m] = C[(int64_t)bc_index(k0 - 2 + m, a.nz, a.bcz) * plane + (int64_t)jc * a.nx + ic];
+    for (int m = 0; m < 6; ++m) q[m] = C[(int64_t)bc_near(k0 - 2 + m, a.nz, a.bcz) * plane + col];
 
     T fz_lo = T(0);
     if (ADV) {
         // flux through the lower z-face of plane k0
         const bool wall = (a.bcz == CH_NOFLUX) && (k0 == 0);
         if (!wall) {
-            const T cm3 = C[(int64_t)bc_index(k0 - 3, a.nz, a.bcz) * plane + (int64_t)jc * a.nx + ic];
-            const int f = (a.bcz == CH_PERIODIC) ? k0 % a.nz : k0;
-            const T wv = w[((int64_t)f * a.ny + jc) * a.nx + ic];
+            const T cm3 = C[(int64_t)bc_near(k0 - 3, a.nz, a.bcz) * plane + col];
+            const T wv = w[(int64_t)k0 * plane + col];
             fz_lo = face_flux(wv, cm3, q[0], q[1], q[2], q[3], q[4], eps);
         }
     }
+    __syncthreads();  // index tables ready
 
-    for (int k = k0, buf = 0; k < kend; ++k, buf ^= 1) {
-        // stage plane k with its x/y halo
-        const T* Ck = C + (int64_t)k * plane;
+    // Planes are staged with asynchronous 4/8-byte copies into a ring of three
+    // buffers: plane k+1 is in flight while plane k is computed, and the
+    // buffer being refilled was last read two planes ago (behind a barrier).
+    auto stage = [&](int kk, int b) {
+        const T* Ck = C + (int64_t)kk * plane;
         for (int e = tid; e < PX * PY; e += kTX * kTY) {
-            const int row = e / PX, col = e - row * PX;
-            const int gi = bc_index(i0 + col - kHalo, a.nx, a.bcx);
-            const int gj = bc_index(j0 + row - kHalo, a.ny, a.bcy);
-            Cs[buf][row][col] = Ck[(int64_t)gj * a.nx + gi];
+            const int row = e / PX, cc = e - row * PX;
+            cp_async_elem(&Cs[b][row][cc], Ck + (int64_t)gj_tab[row] * a.nx + gi_tab[cc]);
+        }
+        cp_async_commit();
+    };
+    stage(k0, 0);
+    for (int k = k0, buf = 0; k < kend; ++k, buf = (buf == 2 ? 0 : buf + 1)) {
+        if (k + 1 < kend) {
+            stage(k + 1, buf == 2 ? 0 : buf + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         // prefetch the next queue entry C(k + 4)
-        const T qnext = C[(int64_t)bc_index(k + 4, a.nz, a.bcz) * plane + (int64_t)jc * a.nx + ic];
+        const T qnext = C[(int64_t)bc_near(k + 4, a.nz, a.bcz) * plane + col];
         __syncthreads();
 
         const int cy = ty + kHalo, cx = tx + kHalo;
         T fz_up = T(0);
         if (ADV) {
+            const int64_t kp = (int64_t)k * a.ny;
             // x: flux through this cell's lower face (face i)
             {
-                const bool wall = (a.bcx == CH_NOFLUX) && (i <= 0 || i >= a.nx);
                 T f = T(0);
-                if (!wall) {
-                    const int fi = (a.bcx == CH_PERIODIC) ? bc_index(i, a.nx, CH_PERIODIC) : i;
-                    const T uv = u[((int64_t)k * a.ny + jc) * a.nfx + fi];
+                if (!wall_x) {
+                    const T uv = u[(kp + jc) * a.nfx + fi];
                     f = face_flux(uv, Cs[buf][cy][cx - 3], Cs[buf][cy][cx - 2], Cs[buf][cy][cx - 1],
                                   Cs[buf][cy][cx], Cs[buf][cy][cx + 1], Cs[buf][cy][cx + 2], eps);
                 }
@@ -159,38 +215,29 @@ ch_explicit_rhs(const T* __restrict__ C, const T* __restrict__ u, const T* __res
             }
             // y: flux through this cell's lower face (face j)
             {
-                const bool wall = (a.bcy == CH_NOFLUX) && (j <= 0 || j >= a.ny);
                 T f = T(0);
-                if (!wall) {
-                    const int fj = (a.bcy == CH_PERIODIC) ? bc_index(j, a.ny, CH_PERIODIC) : j;
+                if (!wall_y) {
                     const T vv = v[((int64_t)k * a.nfy + fj) * a.nx + ic];
                     f = face_flux(vv, Cs[buf][cy - 3][cx], Cs[buf][cy - 2][cx], Cs[buf][cy - 1][cx],
                                   Cs[buf][cy][cx], Cs[buf][cy + 1][cx], Cs[buf][cy + 2][cx], eps);
                 }
                 Fy[ty][tx] = f;
             }
-            // the tile's extra upper faces: x-face i0+32 of each row (warp 0,
-            // lanes 0..7) and y-face j0+8 of each column (warp 1)
+            // the tile's extra upper faces
             if (ty == 0 && tx < kTY) {
-                const int row = tx, ie = i0 + kTX, je = min(j0 + row, a.ny - 1);
-                const bool wall = (a.bcx == CH_NOFLUX) && (ie >= a.nx);
                 T f = T(0);
-                if (!wall) {
-                    const int fi = (a.bcx == CH_PERIODIC) ? bc_index(ie, a.nx, CH_PERIODIC) : ie;
-                    const T uv = u[((int64_t)k * a.ny + je) * a.nfx + fi];
-                    const int yy = row + kHalo, xx = kTX + kHalo;
+                if (!wall_xe) {
+                    const T uv = u[(kp + je_row) * a.nfx + fie];
+                    const int yy = tx + kHalo, xx = kTX + kHalo;
                     f = face_flux(uv, Cs[buf][yy][xx - 3], Cs[buf][yy][xx - 2], Cs[buf][yy][xx - 1],
                                   Cs[buf][yy][xx], Cs[buf][yy][xx + 1], Cs[buf][yy][xx + 2], eps);
                 }
-                Fx[row][kTX] = f;
+                Fx[tx][kTX] = f;
             }
             if (ty == 1) {
-                const int je = j0 + kTY;
-                const bool wall = (a.bcy == CH_NOFLUX) && (je >= a.ny);
                 T f = T(0);
-                if (!wall) {
-                    const int fj = (a.bcy == CH_PERIODIC) ? bc_index(je, a.ny, CH_PERIODIC) : je;
-                    const T vv = v[((int64_t)k * a.nfy + fj) * a.nx + ic];
+                if (!wall_ye) {
+                    const T vv = v[((int64_t)k * a.nfy + fje) * a.nx + ic];
                     const int yy = kTY + kHalo, xx = cx;
                     f = face_flux(vv, Cs[buf][yy - 3][xx], Cs[buf][yy - 2][xx], Cs[buf][yy - 1][xx],
                                   Cs[buf][yy][xx], Cs[buf][yy + 1][xx], Cs[buf][yy + 2][xx], eps);
@@ -201,8 +248,8 @@ ch_explicit_rhs(const T* __restrict__ C, const T* __restrict__ u, const T* __res
             {
                 const bool wall = (a.bcz == CH_NOFLUX) && (k + 1 >= a.nz);
                 if (!wall) {
-                    const int f = (a.bcz == CH_PERIODIC) ? (k + 1) % a.nz : k + 1;
-                    const T wv = w[((int64_t)f * a.ny + jc) * a.nx + ic];
+                    const int f = (k + 1 < a.nz) ? k + 1 : 0;
+                    const T wv = w[(int64_t)f * plane + col];
                     fz_up = face_flux(wv, q[0], q[1], q[2], q[3], q[4], q[5], eps);
                 }
             }
@@ -211,25 +258,24 @@ ch_explicit_rhs(const T* __restrict__ C, const T* __restrict__ u, const T* __res
 
         // M lap(psi'(C)), 7-point central (Sec. 3)
         const T c0 = Cs[buf][cy][cx];
-        const T p0 = psi_p(c0);
         const T lap = (psi_p(Cs[buf][cy][cx - 1]) + psi_p(Cs[buf][cy][cx + 1]) + psi_p(Cs[buf][cy - 1][cx]) +
-                       psi_p(Cs[buf][cy + 1][cx]) + psi_p(q[1]) + psi_p(q[3]) - T(6) * p0) *
-                      T(a.inv_h2);
+                       psi_p(Cs[buf][cy + 1][cx]) + psi_p(q[1]) + psi_p(q[3]) - T(6) * psi_p(c0)) *
+                      a.inv_h2;
         // raw [1,-4,6,-4,1] sums of A_x + A_y + A_z (Eq. eq-a3d)
         const T ax = Cs[buf][cy][cx - 2] + Cs[buf][cy][cx + 2] - T(4) * (Cs[buf][cy][cx - 1] + Cs[buf][cy][cx + 1]);
         const T ay = Cs[buf][cy - 2][cx] + Cs[buf][cy + 2][cx] - T(4) * (Cs[buf][cy - 1][cx] + Cs[buf][cy + 1][cx]);
         const T az = q[0] + q[4] - T(4) * (q[1] + q[3]);
         const T astar = ax + ay + az + T(18) * c0;
 
-        T H = T(a.mob) * lap;
+        T H = a.mob * lap;
         if (ADV) {
             const T div = (Fx[ty][tx + 1] - Fx[ty][tx]) + (Fy[ty + 1][tx] - Fy[ty][tx]) + (fz_up - fz_lo);
-            H -= div * T(a.inv_h);
+            H -= div * a.inv_h;
         }
         if (in_xy) {
             const int64_t idx = (int64_t)k * plane + (int64_t)j * a.nx + i;
-            T rhs = T(a.dtg) * H - T(a.impl) * astar;
-            if (a.has_prev) rhs += T(a.dtr) * Hprev[idx];
+            T rhs = a.dtg * H - a.impl * astar;
+            if (a.has_prev) rhs += a.dtr * Hprev[idx];
             Hout[idx] = H;
             r[idx] = rhs;
         }
@@ -245,131 +291,274 @@ ch_explicit_rhs(const T* __restrict__ C, const T* __restrict__ u, const T* __res
 // Line solves.  The matrix (I + c A_d) is the same for every line of a
 // direction, so its banded LU factors (and, for periodic directions, the
 // rank-4 Woodbury correction of the corner entries) are computed once on the
-// host in FP64.  Per line: forward sweep (also accumulating the Woodbury dot
-// products W^T r), then backward sweep emitting x_band - Z s.
+// host in FP64:
+//   forward  y_j = r_j - l1_j y_{j-1} - l2_j y_{j-2},   z_j = y_j / u0_j
+//   backward x_j = z_j - (u1_j/u0_j) x_{j+1} - (u2_j/u0_j) x_{j+2}
+//   periodic out_j = x_j - Z_j . s,  s = S (W^T r)   (Woodbury)
+// One warp solves one line.  Lane l owns the M consecutive rows
+// [l M, l M + M) in registers.  Both order-2 recurrences are affine maps of
+// the state (y_j, y_{j-1}) (resp. (x_j, x_{j+1})); each lane first runs its
+// chunk from a zero state, a 5-step warp-shuffle scan composes the chunks
+// (the 2x2 transfer matrices of every lane span are coefficient-only and
+// precomputed on the host), and each lane then reruns its chunk from the
+// correct incoming state.  Rows past n are padding with zero coefficients.
 // ---------------------------------------------------------------------------
 template <typename T>
-struct Coef {
-    const T* __restrict__ l1;
-    const T* __restrict__ l2;
-    const T* __restrict__ u1;
-    const T* __restrict__ u2;
-    const T* __restrict__ dinv;
-    const T* __restrict__ W;
-    const T* __restrict__ Z;
-    const T* __restrict__ S;
+struct WCoef {
+    const T* __restrict__ fwd;  // [M][32][4]: l1, l2, 1/u0, 0      (row j = lane*M + i at [i][lane])
+    const T* __restrict__ bwd;  // [M][32][2]: u1/u0, u2/u0
+    const T* __restrict__ W;    // [M][32][4]  periodic only
+    const T* __restrict__ Z;    // [M][32][4]  periodic only
+    const T* __restrict__ Pf;   // [5][32][4]  forward span matrices, row-major 2x2
+    const T* __restrict__ Pb;   // [5][32][4]  backward span matrices
+    const T* __restrict__ S;    // [4][4]      periodic only
     int n;
     int periodic;
 };
 
-// Solve one line held in shared memory at s[j * stride], in place.
 template <typename T>
-__device__ __forceinline__ void sweep_line(T* s, int stride, const Coef<T>& cf) {
-    const int n = cf.n;
+struct V4 {
+    T x, y, z, w;
+};
+
+__device__ __forceinline__ V4<float> ld4(const float* p) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ V4<double> ld4(const double* p) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    return {a.x, a.y, b.x, b.y};
+}
+__device__ __forceinline__ void ld2(const float* p, float& a, float& b) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    a = v.x;
+    b = v.y;
+}
+__device__ __forceinline__ void ld2(const double* p, double& a, double& b) {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    a = v.x;
+    b = v.y;
+}
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Solve the line whose rows lane*M .. lane*M+M-1 are in v[] (rhs in, solution out).
+template <typename T, int M>
+__device__ __forceinline__ void warp_line_solve(T (&v)[M], const WCoef<T>& cf, int lane) {
+    const bool per = cf.periodic;
+    // ---- forward elimination: zero-start pass over the chunk
     T y1 = T(0), y2 = T(0);
     T acc0 = T(0), acc1 = T(0), acc2 = T(0), acc3 = T(0);
-    if (cf.periodic) {
-        for (int jj = 0; jj < n; ++jj) {
-            const T rj = s[jj * stride];
-            const T yj = rj - __ldg(cf.l1 + jj) * y1 - __ldg(cf.l2 + jj) * y2;
-            const T* Wj = cf.W + 4 * jj;
-            acc0 += __ldg(Wj + 0) * rj;
-            acc1 += __ldg(Wj + 1) * rj;
-            acc2 += __ldg(Wj + 2) * rj;
-            acc3 += __ldg(Wj + 3) * rj;
-            s[jj * stride] = yj;
-            y2 = y1;
-            y1 = yj;
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        const V4<T> c = ld4(cf.fwd + (i * 32 + lane) * 4);
+        const T y = (v[i] - c.y * y2) - c.x * y1;
+        y2 = y1;
+        y1 = y;
+        if (per) {
+            const V4<T> w = ld4(cf.W + (i * 32 + lane) * 4);
+            acc0 += w.x * v[i];
+            acc1 += w.y * v[i];
+            acc2 += w.z * v[i];
+            acc3 += w.w * v[i];
+        }
+    }
+    // inclusive scan of the chunk end states over lanes 0..lane
+    T q0 = y1, q1 = y2;
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int d = 1 << s;
+        const T o0 = __shfl_up_sync(kFull, q0, d), o1 = __shfl_up_sync(kFull, q1, d);
+        if (lane >= d) {
+            const V4<T> P = ld4(cf.Pf + (s * 32 + lane) * 4);
+            q0 += P.x * o0 + P.y * o1;
+            q1 += P.z * o0 + P.w * o1;
+        }
+    }
+    y1 = __shfl_up_sync(kFull, q0, 1);
+    y2 = __shfl_up_sync(kFull, q1, 1);
+    if (lane == 0) y1 = y2 = T(0);
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        const V4<T> c = ld4(cf.fwd + (i * 32 + lane) * 4);
+        const T y = (v[i] - c.y * y2) - c.x * y1;
+        y2 = y1;
+        y1 = y;
+        v[i] = y * c.z;
+    }
+    // ---- Woodbury right-hand side s = S W^T r (warp reduction)
+    T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+    if (per) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            acc0 += __shfl_xor_sync(kFull, acc0, o);
+            acc1 += __shfl_xor_sync(kFull, acc1, o);
+            acc2 += __shfl_xor_sync(kFull, acc2, o);
+            acc3 += __shfl_xor_sync(kFull, acc3, o);
+        }
+        const V4<T> r0 = ld4(cf.S), r1 = ld4(cf.S + 4), r2 = ld4(cf.S + 8), r3 = ld4(cf.S + 12);
+        s0 = r0.x * acc0 + r0.y * acc1 + r0.z * acc2 + r0.w * acc3;
+        s1 = r1.x * acc0 + r1.y * acc1 + r1.z * acc2 + r1.w * acc3;
+        s2 = r2.x * acc0 + r2.y * acc1 + r2.z * acc2 + r2.w * acc3;
+        s3 = r3.x * acc0 + r3.y * acc1 + r3.z * acc2 + r3.w * acc3;
+    }
+    // ---- back substitution: zero-start pass over the chunk (bottom row first)
+    T x1 = T(0), x2 = T(0);
+#pragma unroll
+    for (int i = M - 1; i >= 0; --i) {
+        T u1, u2;
+        ld2(cf.bwd + (i * 32 + lane) * 2, u1, u2);
+        const T x = (v[i] - u2 * x2) - u1 * x1;
+        x2 = x1;
+        x1 = x;
+    }
+    // inclusive scan from the last lane down
+    q0 = x1;
+    q1 = x2;
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int d = 1 << s;
+        const T o0 = __shfl_down_sync(kFull, q0, d), o1 = __shfl_down_sync(kFull, q1, d);
+        if (lane + d < 32) {
+            const V4<T> P = ld4(cf.Pb + (s * 32 + lane) * 4);
+            q0 += P.x * o0 + P.y * o1;
+            q1 += P.z * o0 + P.w * o1;
+        }
+    }
+    x1 = __shfl_down_sync(kFull, q0, 1);
+    x2 = __shfl_down_sync(kFull, q1, 1);
+    if (lane == 31) x1 = x2 = T(0);
+#pragma unroll
+    for (int i = M - 1; i >= 0; --i) {
+        T u1, u2;
+        ld2(cf.bwd + (i * 32 + lane) * 2, u1, u2);
+        const T x = (v[i] - u2 * x2) - u1 * x1;
+        x2 = x1;
+        x1 = x;
+        T o = x;
+        if (per) {
+            const V4<T> z = ld4(cf.Z + (i * 32 + lane) * 4);
+            o -= z.x * s0 + z.y * s1 + z.z * s2 + z.w * s3;
+        }
+        v[i] = o;
+    }
+}
+
+// x-lines (contiguous): one warp per line, lane chunks read and written
+// directly (16-byte vectors when the line and chunk are aligned).
+template <typename T, int M>
+__global__ void __launch_bounds__(256)
+ch_solve_x(T* __restrict__ a, int64_t nlines, int nx, WCoef<T> cf) {
+    const int lane = threadIdx.x & 31;
+    const int64_t line = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (line >= nlines) return;  // whole warp
+    T* p = a + line * nx;
+    const int j0 = lane * M;
+    T v[M];
+    constexpr int VEC = 16 / sizeof(T);
+    const bool vec = (M % VEC == 0) && (nx % VEC == 0) && (j0 + M <= nx);
+    if (vec) {
+#pragma unroll
+        for (int i = 0; i < M; i += VEC) {
+            if (sizeof(T) == 4) {
+                const float4 t = *reinterpret_cast<const float4*>(p + j0 + i);
+                v[i] = (T)t.x; v[i + 1] = (T)t.y; v[i + 2] = (T)t.z; v[i + 3] = (T)t.w;
+            } else {
+                const double2 t = *reinterpret_cast<const double2*>(p + j0 + i);
+                v[i] = (T)t.x; v[i + 1] = (T)t.y;
+            }
         }
     } else {
-        for (int jj = 0; jj < n; ++jj) {
-            const T yj = s[jj * stride] - __ldg(cf.l1 + jj) * y1 - __ldg(cf.l2 + jj) * y2;
-            s[jj * stride] = yj;
-            y2 = y1;
-            y1 = yj;
-        }
+#pragma unroll
+        for (int i = 0; i < M; ++i) v[i] = (j0 + i < nx) ? p[j0 + i] : T(0);
     }
-    T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-    if (cf.periodic) {
-        const T* S = cf.S;
-        s0 = __ldg(S + 0) * acc0 + __ldg(S + 1) * acc1 + __ldg(S + 2) * acc2 + __ldg(S + 3) * acc3;
-        s1 = __ldg(S + 4) * acc0 + __ldg(S + 5) * acc1 + __ldg(S + 6) * acc2 + __ldg(S + 7) * acc3;
-        s2 = __ldg(S + 8) * acc0 + __ldg(S + 9) * acc1 + __ldg(S + 10) * acc2 + __ldg(S + 11) * acc3;
-        s3 = __ldg(S + 12) * acc0 + __ldg(S + 13) * acc1 + __ldg(S + 14) * acc2 + __ldg(S + 15) * acc3;
-    }
-    T x1 = T(0), x2 = T(0);
-    for (int jj = n - 1; jj >= 0; --jj) {
-        const T xj = (s[jj * stride] - __ldg(cf.u1 + jj) * x1 - __ldg(cf.u2 + jj) * x2) * __ldg(cf.dinv + jj);
-        T out = xj;
-        if (cf.periodic) {
-            const T* Zj = cf.Z + 4 * jj;
-            out -= __ldg(Zj + 0) * s0 + __ldg(Zj + 1) * s1 + __ldg(Zj + 2) * s2 + __ldg(Zj + 3) * s3;
+    warp_line_solve<T, M>(v, cf, lane);
+    if (vec) {
+#pragma unroll
+        for (int i = 0; i < M; i += VEC) {
+            if (sizeof(T) == 4) {
+                float4 t;
+                t.x = (float)v[i]; t.y = (float)v[i + 1]; t.z = (float)v[i + 2]; t.w = (float)v[i + 3];
+                *reinterpret_cast<float4*>(p + j0 + i) = t;
+            } else {
+                double2 t;
+                t.x = (double)v[i]; t.y = (double)v[i + 1];
+                *reinterpret_cast<double2*>(p + j0 + i) = t;
+            }
         }
-        s[jj * stride] = out;
-        x2 = x1;
-        x1 = xj;
+    } else {
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+            if (j0 + i < nx) p[j0 + i] = v[i];
     }
 }
 
-constexpr int kSolveThreads = 128;
+// y- or z-lines (strided).  A CTA of 16 warps owns 32 consecutive x of one
+// outer position: the [n][32] tile is staged through shared memory with
+// coalesced 32-wide rows; element (row j, column c) sits at j*32 + (c ^ (j/M)
+// mod 32), so both the row-wise staging and the per-lane chunk reads of one
+// column are bank-conflict free.  Warp w solves columns w, w + W, ... (W
+// warps per CTA: 16 for short lines, 8 for long ones, which need more
+// registers per lane).  With UPDATE the solved increment is added to C
+// (Eq. eq-fac-3: q^{l+1} = q^l + dq) and non-finite results raise a flag.
+template <typename T, int M>
+struct YZShape {
+    static constexpr bool kLong = M * sizeof(T) >= 64;
+    static constexpr int kWarps = kLong ? 8 : 16;
+    static constexpr int kMinBlocks = kLong ? 1 : 2;
+};
 
-// x-lines (contiguous).  A CTA stages `lines` rows of length nx in shared
-// memory (row stride nx+1 to spread banks), warp 0 sweeps one line per lane.
-template <typename T>
-__global__ void __launch_bounds__(kSolveThreads)
-ch_solve_x(T* __restrict__ a, int64_t nlines, int nx, int lines, Coef<T> cf) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* s = reinterpret_cast<T*>(smem_raw);
-    const int stride = nx + 1;
-    const int64_t line0 = (int64_t)blockIdx.x * lines;
-    const int nl = (int)min((int64_t)lines, nlines - line0);
-    for (int l = 0; l < nl; ++l) {
-        const T* src = a + (line0 + l) * nx;
-        for (int x = threadIdx.x; x < nx; x += kSolveThreads) s[l * stride + x] = src[x];
-    }
-    __syncthreads();
-    if (threadIdx.x < nl) sweep_line(s + threadIdx.x * stride, 1, cf);
-    __syncthreads();
-    for (int l = 0; l < nl; ++l) {
-        T* dst = a + (line0 + l) * nx;
-        for (int x = threadIdx.x; x < nx; x += kSolveThreads) dst[x] = s[l * stride + x];
-    }
-}
-
-// y- or z-lines (strided).  A CTA owns `lanes` consecutive x of one (z) or
-// (y) position; row jj of its tile is `lanes` contiguous values, so loads
-// and stores are coalesced.  With UPDATE, the solved increment is added to C
-// (Eq. eq-fac-3: q^{l+1} = q^l + dq) and non-finite values raise a flag.
-template <typename T, bool UPDATE>
-__global__ void __launch_bounds__(kSolveThreads)
+template <typename T, int M, bool UPDATE>
+__global__ void __launch_bounds__(YZShape<T, M>::kWarps * 32, YZShape<T, M>::kMinBlocks)
 ch_solve_yz(T* __restrict__ a, T* __restrict__ Cf, int nx, int64_t outer_stride, int64_t line_stride,
-            int lanes, Coef<T> cf, unsigned int* status) {
+            WCoef<T> cf, unsigned int* status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* s = reinterpret_cast<T*>(smem_raw);
+    constexpr int kYZWarps = YZShape<T, M>::kWarps;
     const int n = cf.n;
-    const int xblocks = (nx + lanes - 1) / lanes;
+    const int xblocks = (nx + 31) >> 5;
     const int xb = blockIdx.x % xblocks;
     const int64_t outer = blockIdx.x / xblocks;
-    const int i0 = xb * lanes;
-    const int nl = min(lanes, nx - i0);
+    const int i0 = xb * 32;
+    const int nl = min(32, nx - i0);
     const int64_t base = outer * outer_stride + i0;
-    const int rows_per_pass = kSolveThreads / lanes;
-    const int lane = threadIdx.x % lanes, rsub = threadIdx.x / lanes;
-    for (int jj = rsub; jj < n; jj += rows_per_pass)
-        if (lane < nl) s[jj * lanes + lane] = a[base + (int64_t)jj * line_stride + lane];
+    const int tid = threadIdx.x, c = tid & 31, r0 = tid >> 5;
+    auto slot = [&](int j, int col) { return j * 32 + (col ^ ((j / M) & 31)); };
+    // stage rows asynchronously (zero padding past n and past the ragged x edge)
+#pragma unroll
+    for (int j = r0; j < 32 * M; j += kYZWarps) {
+        if (j < n && c < nl)
+            cp_async_elem(&s[slot(j, c)], a + base + (int64_t)j * line_stride + c);
+        else
+            s[slot(j, c)] = T(0);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
-    if (threadIdx.x < nl) sweep_line(s + threadIdx.x, lanes, cf);
+    const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll 1
+    for (int col = warp; col < 32; col += kYZWarps) {
+        T v[M];
+#pragma unroll
+        for (int i = 0; i < M; ++i) v[i] = s[slot(lane * M + i, col)];
+        warp_line_solve<T, M>(v, cf, lane);
+#pragma unroll
+        for (int i = 0; i < M; ++i) s[slot(lane * M + i, col)] = v[i];
+    }
     __syncthreads();
     bool bad = false;
-    for (int jj = rsub; jj < n; jj += rows_per_pass) {
-        if (lane < nl) {
-            const int64_t idx = base + (int64_t)jj * line_stride + lane;
+#pragma unroll
+    for (int j = r0; j < 32 * M; j += kYZWarps) {
+        if (j < n && c < nl) {
+            const int64_t idx = base + (int64_t)j * line_stride + c;
+            const T d = s[slot(j, c)];
             if (UPDATE) {
-                const T cnew = Cf[idx] + s[jj * lanes + lane];
+                const T cnew = Cf[idx] + d;
                 bad |= !isfinite(cnew);
                 Cf[idx] = cnew;
             } else {
-                a[idx] = s[jj * lanes + lane];
+                a[idx] = d;
             }
         }
     }

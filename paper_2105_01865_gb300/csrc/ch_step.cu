@@ -13,12 +13,14 @@
 
 #include "ch_internal.h"
 #include "ch_kernels.cuh"
+#include "line_tables.h"
 
 using namespace chg;
 
 namespace {
 
 constexpr size_t kAlign = 256;
+constexpr size_t kMaxSmem = 227 * 1024;  // dynamic shared memory per CTA (sm_103a)
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 bool params_valid(const ch_params* p, char* why, size_t wl) {
@@ -56,10 +58,13 @@ bool params_valid(const ch_params* p, char* why, size_t wl) {
                 if (!(f[d][k + 1] > f[d][k])) return bad("coarse face coordinates must increase");
         }
     }
-    // line-solve tiles must fit in shared memory (8 lines of the longest direction)
+    // warp-scan line solves: at most 32 x 32 rows per line; the y/z tile
+    // (32 M rows x 32 columns) must fit in shared memory
     const size_t esz = p->precision == CH_F64 ? 8 : 4;
-    const int64_t nmax = std::max(p->nx + 1, std::max(p->ny, p->nz));
-    if ((size_t)nmax * 8 * esz > 200 * 1024) return bad("a line is too long for the shared-memory line solve");
+    if (p->nx > 1024 || p->ny > 1024 || p->nz > 1024) return bad("lines longer than 1024 cells are not supported");
+    for (int64_t n : {p->ny, p->nz})
+        if ((size_t)32 * warp_chunk((int)n) * 32 * esz > kMaxSmem)
+            return bad("y/z line too long for the shared-memory tile in this precision (FP64: <= 512)");
     return true;
 }
 
@@ -101,186 +106,74 @@ Layout layout(const ch_params* p) {
     return L;
 }
 
-// Banded LU without pivoting of a pentadiagonal matrix given by its bands
-// e (j, j-2), c (j, j-1), d (j, j), a (j, j+1), b (j, j+2).
-struct BandLU {
-    std::vector<double> l1, l2, u0, u1, u2;
-};
-
-BandLU band_lu(const std::vector<double>& e, const std::vector<double>& c, const std::vector<double>& d,
-               const std::vector<double>& a, const std::vector<double>& b) {
-    const int n = (int)d.size();
-    BandLU f;
-    f.l1.assign(n, 0.0);
-    f.l2.assign(n, 0.0);
-    f.u0.assign(n, 0.0);
-    f.u1.assign(n, 0.0);
-    f.u2.assign(n, 0.0);
-    for (int j = 0; j < n; ++j) {
-        if (j >= 2) f.l2[j] = e[j] / f.u0[j - 2];
-        if (j >= 1) f.l1[j] = (c[j] - (j >= 2 ? f.l2[j] * f.u1[j - 2] : 0.0)) / f.u0[j - 1];
-        f.u0[j] = d[j] - (j >= 1 ? f.l1[j] * f.u1[j - 1] : 0.0) - (j >= 2 ? f.l2[j] * f.u2[j - 2] : 0.0);
-        f.u1[j] = (j + 1 < n ? a[j] : 0.0) - (j >= 1 ? f.l1[j] * f.u2[j - 1] : 0.0);
-        f.u2[j] = (j + 2 < n) ? b[j] : 0.0;
-    }
-    return f;
-}
-
-std::vector<double> band_solve(const BandLU& f, std::vector<double> x) {
-    const int n = (int)x.size();
-    for (int j = 0; j < n; ++j)
-        x[j] -= (j >= 1 ? f.l1[j] * x[j - 1] : 0.0) + (j >= 2 ? f.l2[j] * x[j - 2] : 0.0);
-    for (int j = n - 1; j >= 0; --j) {
-        double s = x[j];
-        if (j + 1 < n) s -= f.u1[j] * x[j + 1];
-        if (j + 2 < n) s -= f.u2[j] * x[j + 2];
-        x[j] = s / f.u0[j];
-    }
-    return x;
-}
-
-bool invert4(const double* A, double* out) {
-    double M[4][8];
-    for (int i = 0; i < 4; ++i)
-        for (int j = 0; j < 8; ++j) M[i][j] = j < 4 ? A[i * 4 + j] : (j - 4 == i ? 1.0 : 0.0);
-    for (int col = 0; col < 4; ++col) {
-        int piv = col;
-        for (int i = col + 1; i < 4; ++i)
-            if (std::fabs(M[i][col]) > std::fabs(M[piv][col])) piv = i;
-        if (M[piv][col] == 0.0) return false;
-        for (int j = 0; j < 8; ++j) std::swap(M[col][j], M[piv][j]);
-        const double inv = 1.0 / M[col][col];
-        for (int j = 0; j < 8; ++j) M[col][j] *= inv;
-        for (int i = 0; i < 4; ++i) {
-            if (i == col) continue;
-            const double f = M[i][col];
-            for (int j = 0; j < 8; ++j) M[i][j] -= f * M[col][j];
-        }
-    }
-    for (int i = 0; i < 4; ++i)
-        for (int j = 0; j < 4; ++j) out[i * 4 + j] = M[i][j + 4];
-    return true;
-}
-
-// Host FP64 coefficients of (I + c kappa B) for one direction: B applies
-// [1,-4,6,-4,1] with wrapped (periodic) or mirrored (wall) neighbours.
-// Returns the arrays l1, l2, u1, u2, dinv (n each) and, when periodic,
-// W (n x 4), Z (n x 4), S (4 x 4) of the Woodbury correction of the corners.
-std::vector<double> line_coefficients(int n, int bc, double ck) {
-    std::vector<double> e(n, 0.0), c(n, 0.0), d(n, 1.0), a(n, 0.0), b(n, 0.0);
-    // corner (out-of-band) entries for the periodic case: (row, col, value)
-    std::vector<std::tuple<int, int, double>> corner;
-    const double stencil[5] = {1.0, -4.0, 6.0, -4.0, 1.0};
-    for (int i = 0; i < n; ++i) {
-        for (int s = -2; s <= 2; ++s) {
-            int j = i + s;
-            if (bc == CH_PERIODIC) {
-                j = ((j % n) + n) % n;
-            } else {
-                if (j < 0) j = -1 - j;
-                if (j >= n) j = 2 * n - 1 - j;
-            }
-            const double val = ck * stencil[s + 2];
-            const int off = j - i;
-            switch (off) {
-                case -2: e[i] += val; break;
-                case -1: c[i] += val; break;
-                case 0: d[i] += val; break;
-                case 1: a[i] += val; break;
-                case 2: b[i] += val; break;
-                default: corner.emplace_back(i, j, val);
-            }
-        }
-    }
-    const BandLU f = band_lu(e, c, d, a, b);
-    std::vector<double> out;
-    out.reserve(5 * n + 8 * n + 16);
-    out.insert(out.end(), f.l1.begin(), f.l1.end());
-    out.insert(out.end(), f.l2.begin(), f.l2.end());
-    out.insert(out.end(), f.u1.begin(), f.u1.end());
-    out.insert(out.end(), f.u2.begin(), f.u2.end());
-    for (int j = 0; j < n; ++j) out.push_back(1.0 / f.u0[j]);
-    if (bc != CH_PERIODIC) return out;
-    // Woodbury: M = Mb + U V^T with U = [e_r] for the corner rows r in R,
-    // V^T = the corner part of those rows.  M^-1 r = y - Z (I + V^T Z)^-1 V^T y,
-    // y = Mb^-1 r, Z = Mb^-1 U; V^T y = W^T r with W = Mb^-T V.
-    const int R[4] = {0, 1, n - 2, n - 1};
-    std::vector<double> Vt(4 * (size_t)n, 0.0);
-    for (auto& t : corner) {
-        const int row = std::get<0>(t);
-        int m = -1;
-        for (int q = 0; q < 4; ++q)
-            if (R[q] == row) m = q;
-        Vt[(size_t)m * n + std::get<1>(t)] += std::get<2>(t);
-    }
-    // transpose band for Mb^-T
-    std::vector<double> et(n, 0.0), ctt(n, 0.0), at(n, 0.0), bt(n, 0.0);
-    for (int j = 0; j < n; ++j) {
-        if (j >= 2) et[j] = b[j - 2];
-        if (j >= 1) ctt[j] = a[j - 1];
-        if (j + 1 < n) at[j] = c[j + 1];
-        if (j + 2 < n) bt[j] = e[j + 2];
-    }
-    const BandLU ft = band_lu(et, ctt, d, at, bt);
-    std::vector<double> W(4 * (size_t)n), Z(4 * (size_t)n);
-    for (int m = 0; m < 4; ++m) {
-        std::vector<double> vcol(Vt.begin() + (size_t)m * n, Vt.begin() + (size_t)(m + 1) * n);
-        std::vector<double> wcol = band_solve(ft, vcol);
-        std::vector<double> ucol(n, 0.0);
-        ucol[R[m]] = 1.0;
-        std::vector<double> zcol = band_solve(f, ucol);
-        for (int j = 0; j < n; ++j) {
-            W[(size_t)j * 4 + m] = wcol[j];
-            Z[(size_t)j * 4 + m] = zcol[j];
-        }
-    }
-    double cap[16], S[16];
-    for (int p = 0; p < 4; ++p)
-        for (int q = 0; q < 4; ++q) {
-            double s = (p == q) ? 1.0 : 0.0;
-            for (int j = 0; j < n; ++j) s += Vt[(size_t)p * n + j] * Z[(size_t)j * 4 + q];
-            cap[p * 4 + q] = s;
-        }
-    if (!invert4(cap, S)) return {};
-    out.insert(out.end(), W.begin(), W.end());
-    out.insert(out.end(), Z.begin(), Z.end());
-    out.insert(out.end(), S, S + 16);
-    return out;
-}
-
 template <typename T>
-Coef<T> coef_of(const LineCoefs& c) {
-    Coef<T> k;
-    k.l1 = (const T*)c.l1;
-    k.l2 = (const T*)c.l2;
-    k.u1 = (const T*)c.u1;
-    k.u2 = (const T*)c.u2;
-    k.dinv = (const T*)c.dinv;
-    k.W = (const T*)c.W;
-    k.Z = (const T*)c.Z;
-    k.S = (const T*)c.S;
-    k.n = c.n;
-    k.periodic = c.periodic;
+WCoef<T> wcoef(const LineTables& lt) {
+    const WarpLayout L = warp_layout(lt.M);
+    const T* b = (const T*)lt.base;
+    WCoef<T> k;
+    k.fwd = b + L.fwd;
+    k.bwd = b + L.bwd;
+    k.W = b + L.W;
+    k.Z = b + L.Z;
+    k.Pf = b + L.Pf;
+    k.Pb = b + L.Pb;
+    k.S = b + L.S;
+    k.n = lt.n;
+    k.periodic = lt.periodic;
     return k;
 }
 
-int solve_x_lines(int nx, size_t esz) {
-    // lines per CTA for the x solve: up to 32 rows of nx+1 values in <= 96 KB
-    int lines = (int)std::min<size_t>(32, (96 * 1024) / ((size_t)(nx + 1) * esz));
-    return std::max(lines, 1);
+template <typename T, int M>
+int launch_solves_m(ch_handle* h, int l, int dir, cudaEvent_t ev_after) {
+    const int nx = (int)h->n[0], ny = (int)h->n[1], nz = (int)h->n[2];
+    T* r = (T*)h->r;
+    const WCoef<T> cf = wcoef<T>(h->lines[dir][l]);
+    if (dir == 0) {
+        const int64_t nlines = (int64_t)ny * nz;
+        constexpr int wpb = 8;
+        ch_solve_x<T, M><<<(unsigned)((nlines + wpb - 1) / wpb), wpb * 32, 0, h->stream>>>(r, nlines, nx, cf);
+    } else {
+        const unsigned xblocks = (unsigned)((nx + 31) / 32);
+        const size_t shm = (size_t)32 * M * 32 * sizeof(T);
+        if (dir == 1)
+            ch_solve_yz<T, M, false><<<xblocks * (unsigned)nz, YZShape<T, M>::kWarps * 32, shm, h->stream>>>(
+                r, nullptr, nx, (int64_t)nx * ny, nx, cf, h->status);
+        else
+            ch_solve_yz<T, M, true><<<xblocks * (unsigned)ny, YZShape<T, M>::kWarps * 32, shm, h->stream>>>(
+                r, (T*)h->C, nx, nx, (int64_t)nx * ny, cf, h->status);
+    }
+    CHG_CUDA(h, cudaGetLastError());
+    if (ev_after) CHG_CUDA(h, cudaEventRecord(ev_after, h->stream));
+    return CH_OK;
 }
 
-int solve_yz_lanes(int n, size_t esz) {
-    int lanes = 32;
-    while (lanes > 8 && (size_t)n * lanes * esz > 96 * 1024) lanes /= 2;
-    return lanes;
+template <typename T>
+int launch_solve(ch_handle* h, int l, int dir, cudaEvent_t ev_after) {
+    switch (h->lines[dir][l].M) {
+        case 1: return launch_solves_m<T, 1>(h, l, dir, ev_after);
+        case 2: return launch_solves_m<T, 2>(h, l, dir, ev_after);
+        case 4: return launch_solves_m<T, 4>(h, l, dir, ev_after);
+        case 8: return launch_solves_m<T, 8>(h, l, dir, ev_after);
+        case 16: return launch_solves_m<T, 16>(h, l, dir, ev_after);
+        case 32: return launch_solves_m<T, 32>(h, l, dir, ev_after);
+        default: return fail(h, CH_EINVAL, "unsupported line length");
+    }
+}
+
+template <typename T, int M>
+int set_attrs_m(ch_handle* h) {
+    const int shm = (int)((size_t)32 * M * 32 * sizeof(T));
+    if ((size_t)shm > kMaxSmem) return CH_OK;  // never launched for this precision
+    CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_yz<T, M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
+    CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_yz<T, M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
+    return CH_OK;
 }
 
 template <typename T>
 int launch_substep(ch_handle* h, int l, cudaEvent_t* ev = nullptr) {
     const ch_params& p = h->p;
     const int nx = (int)h->n[0], ny = (int)h->n[1], nz = (int)h->n[2];
-    RhsArgs a;
+    RhsArgs<T> a;
     a.nx = nx;
     a.ny = ny;
     a.nz = nz;
@@ -290,15 +183,16 @@ int launch_substep(ch_handle* h, int l, cudaEvent_t* ev = nullptr) {
     a.nfx = (int)h->nf[0];
     a.nfy = (int)h->nf[1];
     a.nfz = (int)h->nf[2];
-    a.inv_h = 1.0 / p.h;
-    a.inv_h2 = 1.0 / (p.h * p.h);
-    a.mob = 1.0 / p.pe;
+    const double mob = 1.0 / p.pe;
     const double alpha = kGamma[l] + kRho[l];
     const double kappa = p.w * p.cn * p.cn / (p.h * p.h * p.h * p.h);
-    a.dtg = p.dt * kGamma[l];
-    a.dtr = p.dt * kRho[l];
-    a.impl = alpha * p.dt * a.mob * kappa;
-    a.eps = p.weno_eps;
+    a.inv_h = (T)(1.0 / p.h);
+    a.inv_h2 = (T)(1.0 / (p.h * p.h));
+    a.mob = (T)mob;
+    a.dtg = (T)(p.dt * kGamma[l]);
+    a.dtr = (T)(p.dt * kRho[l]);
+    a.impl = (T)(alpha * p.dt * mob * kappa);
+    a.eps = (T)p.weno_eps;
     a.has_prev = kRho[l] != 0.0;
     T* C = (T*)h->C;
     T* Hout = (T*)h->H[l & 1];
@@ -315,45 +209,24 @@ int launch_substep(ch_handle* h, int l, cudaEvent_t* ev = nullptr) {
     CHG_CUDA(h, cudaGetLastError());
     if (ev) CHG_CUDA(h, cudaEventRecord(ev[1], h->stream));
 
-    // x solve (Eq. eq-fac-1)
-    {
-        const int lines = solve_x_lines(nx, sizeof(T));
-        const int64_t nlines = (int64_t)ny * nz;
-        const size_t shm = (size_t)lines * (nx + 1) * sizeof(T);
-        ch_solve_x<T><<<(unsigned)((nlines + lines - 1) / lines), kSolveThreads, shm, h->stream>>>(
-            r, nlines, nx, lines, coef_of<T>(h->coefs[0][l]));
-        CHG_CUDA(h, cudaGetLastError());
-        if (ev) CHG_CUDA(h, cudaEventRecord(ev[2], h->stream));
-    }
-    // y solve (Eq. eq-fac-2)
-    {
-        const int lanes = solve_yz_lanes(ny, sizeof(T));
-        const size_t shm = (size_t)ny * lanes * sizeof(T);
-        const unsigned blocks = (unsigned)(((nx + lanes - 1) / lanes) * (int64_t)nz);
-        ch_solve_yz<T, false><<<blocks, kSolveThreads, shm, h->stream>>>(
-            r, nullptr, nx, (int64_t)nx * ny, nx, lanes, coef_of<T>(h->coefs[1][l]), h->status);
-        CHG_CUDA(h, cudaGetLastError());
-        if (ev) CHG_CUDA(h, cudaEventRecord(ev[3], h->stream));
-    }
-    // z solve + update (Eq. eq-fac-3)
-    {
-        const int lanes = solve_yz_lanes(nz, sizeof(T));
-        const size_t shm = (size_t)nz * lanes * sizeof(T);
-        const unsigned blocks = (unsigned)(((nx + lanes - 1) / lanes) * (int64_t)ny);
-        ch_solve_yz<T, true><<<blocks, kSolveThreads, shm, h->stream>>>(
-            r, C, nx, nx, (int64_t)nx * ny, lanes, coef_of<T>(h->coefs[2][l]), h->status);
-        CHG_CUDA(h, cudaGetLastError());
-        if (ev) CHG_CUDA(h, cudaEventRecord(ev[4], h->stream));
+    // x solve (Eq. eq-fac-1), y solve (Eq. eq-fac-2), z solve + update (Eq. eq-fac-3)
+    for (int dir = 0; dir < 3; ++dir) {
+        const int rc = launch_solve<T>(h, l, dir, ev ? ev[2 + dir] : nullptr);
+        if (rc != CH_OK) return rc;
     }
     return CH_OK;
 }
 
 template <typename T>
 int set_smem_attrs(ch_handle* h) {
-    CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_yz<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_yz<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    return CH_OK;
+    int rc = CH_OK;
+    if (rc == CH_OK) rc = set_attrs_m<T, 1>(h);
+    if (rc == CH_OK) rc = set_attrs_m<T, 2>(h);
+    if (rc == CH_OK) rc = set_attrs_m<T, 4>(h);
+    if (rc == CH_OK) rc = set_attrs_m<T, 8>(h);
+    if (rc == CH_OK) rc = set_attrs_m<T, 16>(h);
+    if (rc == CH_OK) rc = set_attrs_m<T, 32>(h);
+    return rc;
 }
 
 int launch_step(ch_handle* h) {
@@ -432,7 +305,7 @@ int ch_create(const ch_params* p, void* C, void* work, size_t work_bytes, void* 
     h->launches_per_step = 4 * kRK;
 
     int rc = CH_OK;
-    // line-operator coefficients for every direction and substep
+    // warp-scan line-solve tables for every direction and substep
     {
         const double M = 1.0 / p->pe;
         const double kappa = p->w * p->cn * p->cn / (p->h * p->h * p->h * p->h);
@@ -441,11 +314,18 @@ int ch_create(const ch_params* p, void* C, void* work, size_t work_bytes, void* 
         for (int d = 0; d < 3; ++d)
             for (int l = 0; l < kRK; ++l) {
                 const double ck = (kGamma[l] + kRho[l]) * p->dt * M / 2.0 * kappa;
-                all.push_back(line_coefficients((int)h->n[d], p->bc[d], ck));
-                if (all.back().empty()) {
+                const int n = (int)h->n[d];
+                const LineFactors F = line_factors(n, p->bc[d], ck);
+                if (!F.ok) {
                     free(h);
                     return CH_EINVAL;
                 }
+                const int mch = warp_chunk(n);
+                all.push_back(warp_tables(F, mch));
+                LineTables& lt = h->lines[d][l];
+                lt.n = n;
+                lt.M = mch;
+                lt.periodic = F.periodic;
                 total += align_up(all.back().size() * h->esz);
             }
         if (cudaMalloc(&h->coef_buf, total) != cudaSuccess) {
@@ -454,33 +334,18 @@ int ch_create(const ch_params* p, void* C, void* work, size_t work_bytes, void* 
         }
         std::vector<unsigned char> host(total, 0);
         size_t off = 0;
-        for (int d = 0; d < 3; ++d)
-            for (int l = 0; l < kRK; ++l) {
-                const std::vector<double>& v = all[d * kRK + l];
-                const int n = (int)h->n[d];
-                unsigned char* dst = host.data() + off;
-                for (size_t q = 0; q < v.size(); ++q) {
-                    if (h->esz == 8)
-                        ((double*)dst)[q] = v[q];
-                    else
-                        ((float*)dst)[q] = (float)v[q];
-                }
-                char* base = (char*)h->coef_buf + off;
-                LineCoefs& c = h->coefs[d][l];
-                c.n = n;
-                c.periodic = p->bc[d] == CH_PERIODIC;
-                c.l1 = base;
-                c.l2 = base + (size_t)n * h->esz;
-                c.u1 = base + (size_t)2 * n * h->esz;
-                c.u2 = base + (size_t)3 * n * h->esz;
-                c.dinv = base + (size_t)4 * n * h->esz;
-                if (c.periodic) {
-                    c.W = base + (size_t)5 * n * h->esz;
-                    c.Z = base + (size_t)9 * n * h->esz;
-                    c.S = base + (size_t)13 * n * h->esz;
-                }
-                off += align_up(v.size() * h->esz);
+        for (int q = 0; q < 3 * kRK; ++q) {
+            const std::vector<double>& v = all[q];
+            unsigned char* dst = host.data() + off;
+            for (size_t e = 0; e < v.size(); ++e) {
+                if (h->esz == 8)
+                    ((double*)dst)[e] = v[e];
+                else
+                    ((float*)dst)[e] = (float)v[e];
             }
+            h->lines[q / kRK][q % kRK].base = (char*)h->coef_buf + off;
+            off += align_up(v.size() * h->esz);
+        }
         if (cudaMemcpy(h->coef_buf, host.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) rc = CH_ECUDA;
     }
     if (rc == CH_OK) {

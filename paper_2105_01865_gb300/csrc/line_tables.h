@@ -1,0 +1,281 @@
+// Host-side (FP64) factorisation of the line operators (I + c A_d) of the
+// approximately factorised Crank-Nicolson step (arXiv 2105.01865, Eqs.
+// eq-fac-1..3, with A_d of Eq. eq-a3d) and the tables of the warp-scan line
+// solver.  Plain C++, no CUDA: shared by the library and host-only checks.
+#pragma once
+
+#include <cmath>
+#include <cstddef>
+#include <tuple>
+#include <utility>
+#include <vector>
+
+namespace chg {
+
+constexpr int kBcPeriodic = 0;  // same values as CH_PERIODIC / CH_NOFLUX
+constexpr int kBcNoflux = 1;
+
+// Banded LU without pivoting of a pentadiagonal matrix given by its bands
+// e (j, j-2), c (j, j-1), d (j, j), a (j, j+1), b (j, j+2).
+struct BandLU {
+    std::vector<double> l1, l2, u0, u1, u2;
+};
+
+inline BandLU band_lu(const std::vector<double>& e, const std::vector<double>& c, const std::vector<double>& d,
+                      const std::vector<double>& a, const std::vector<double>& b) {
+    const int n = (int)d.size();
+    BandLU f;
+    f.l1.assign(n, 0.0);
+    f.l2.assign(n, 0.0);
+    f.u0.assign(n, 0.0);
+    f.u1.assign(n, 0.0);
+    f.u2.assign(n, 0.0);
+    for (int j = 0; j < n; ++j) {
+        if (j >= 2) f.l2[j] = e[j] / f.u0[j - 2];
+        if (j >= 1) f.l1[j] = (c[j] - (j >= 2 ? f.l2[j] * f.u1[j - 2] : 0.0)) / f.u0[j - 1];
+        f.u0[j] = d[j] - (j >= 1 ? f.l1[j] * f.u1[j - 1] : 0.0) - (j >= 2 ? f.l2[j] * f.u2[j - 2] : 0.0);
+        f.u1[j] = (j + 1 < n ? a[j] : 0.0) - (j >= 1 ? f.l1[j] * f.u2[j - 1] : 0.0);
+        f.u2[j] = (j + 2 < n) ? b[j] : 0.0;
+    }
+    return f;
+}
+
+inline std::vector<double> band_solve(const BandLU& f, std::vector<double> x) {
+    const int n = (int)x.size();
+    for (int j = 0; j < n; ++j)
+        x[j] -= (j >= 1 ? f.l1[j] * x[j - 1] : 0.0) + (j >= 2 ? f.l2[j] * x[j - 2] : 0.0);
+    for (int j = n - 1; j >= 0; --j) {
+        double s = x[j];
+        if (j + 1 < n) s -= f.u1[j] * x[j + 1];
+        if (j + 2 < n) s -= f.u2[j] * x[j + 2];
+        x[j] = s / f.u0[j];
+    }
+    return x;
+}
+
+inline bool invert4(const double* A, double* out) {
+    double M[4][8];
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 8; ++j) M[i][j] = j < 4 ? A[i * 4 + j] : (j - 4 == i ? 1.0 : 0.0);
+    for (int col = 0; col < 4; ++col) {
+        int piv = col;
+        for (int i = col + 1; i < 4; ++i)
+            if (std::fabs(M[i][col]) > std::fabs(M[piv][col])) piv = i;
+        if (M[piv][col] == 0.0) return false;
+        for (int j = 0; j < 8; ++j) std::swap(M[col][j], M[piv][j]);
+        const double inv = 1.0 / M[col][col];
+        for (int j = 0; j < 8; ++j) M[col][j] *= inv;
+        for (int i = 0; i < 4; ++i) {
+            if (i == col) continue;
+            const double f = M[i][col];
+            for (int j = 0; j < 8; ++j) M[i][j] -= f * M[col][j];
+        }
+    }
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) out[i * 4 + j] = M[i][j + 4];
+    return true;
+}
+
+// Factors of (I + ck B) where B applies [1,-4,6,-4,1] along a line of n
+// cells with wrapped (periodic) or mirrored (wall) neighbours: the band LU
+// with the diagonal folded in (y_j = r_j - l1 y_{j-1} - l2 y_{j-2};
+// x_j = y_j/u0 - (u1/u0) x_{j+1} - (u2/u0) x_{j+2}) and, for periodic lines,
+// the Woodbury correction of the corner entries: out = x - Z S (W^T r).
+struct LineFactors {
+    int n = 0;
+    bool periodic = false;
+    std::vector<double> l1, l2, dinv, u1s, u2s;
+    std::vector<double> W, Z;  // n x 4 each (periodic)
+    double S[16] = {0};
+    bool ok = false;
+};
+
+inline LineFactors line_factors(int n, int bc, double ck) {
+    LineFactors F;
+    F.n = n;
+    F.periodic = bc == kBcPeriodic;
+    std::vector<double> e(n, 0.0), c(n, 0.0), d(n, 1.0), a(n, 0.0), b(n, 0.0);
+    std::vector<std::tuple<int, int, double>> corner;  // out-of-band (row, col, value)
+    const double stencil[5] = {1.0, -4.0, 6.0, -4.0, 1.0};
+    for (int i = 0; i < n; ++i) {
+        for (int s = -2; s <= 2; ++s) {
+            int j = i + s;
+            if (F.periodic) {
+                j = ((j % n) + n) % n;
+            } else {
+                if (j < 0) j = -1 - j;
+                if (j >= n) j = 2 * n - 1 - j;
+            }
+            const double val = ck * stencil[s + 2];
+            switch (j - i) {
+                case -2: e[i] += val; break;
+                case -1: c[i] += val; break;
+                case 0: d[i] += val; break;
+                case 1: a[i] += val; break;
+                case 2: b[i] += val; break;
+                default: corner.emplace_back(i, j, val);
+            }
+        }
+    }
+    const BandLU f = band_lu(e, c, d, a, b);
+    F.l1 = f.l1;
+    F.l2 = f.l2;
+    F.dinv.resize(n);
+    F.u1s.resize(n);
+    F.u2s.resize(n);
+    for (int j = 0; j < n; ++j) {
+        F.dinv[j] = 1.0 / f.u0[j];
+        F.u1s[j] = f.u1[j] / f.u0[j];
+        F.u2s[j] = f.u2[j] / f.u0[j];
+    }
+    if (!F.periodic) {
+        F.ok = true;
+        return F;
+    }
+    // M = Mb + U V^T, U = [e_r] for the corner rows r, V^T = those rows' corner
+    // part.  M^-1 r = y - Z (I + V^T Z)^-1 V^T y with y = Mb^-1 r, Z = Mb^-1 U,
+    // and V^T y = W^T r with W = Mb^-T V.
+    const int R[4] = {0, 1, n - 2, n - 1};
+    std::vector<double> Vt(4 * (size_t)n, 0.0);
+    for (auto& t : corner) {
+        int m = -1;
+        for (int q = 0; q < 4; ++q)
+            if (R[q] == std::get<0>(t)) m = q;
+        Vt[(size_t)m * n + std::get<1>(t)] += std::get<2>(t);
+    }
+    std::vector<double> et(n, 0.0), ct(n, 0.0), at(n, 0.0), bt(n, 0.0);
+    for (int j = 0; j < n; ++j) {
+        if (j >= 2) et[j] = b[j - 2];
+        if (j >= 1) ct[j] = a[j - 1];
+        if (j + 1 < n) at[j] = c[j + 1];
+        if (j + 2 < n) bt[j] = e[j + 2];
+    }
+    const BandLU ft = band_lu(et, ct, d, at, bt);
+    F.W.assign(4 * (size_t)n, 0.0);
+    F.Z.assign(4 * (size_t)n, 0.0);
+    for (int m = 0; m < 4; ++m) {
+        std::vector<double> vcol(Vt.begin() + (size_t)m * n, Vt.begin() + (size_t)(m + 1) * n);
+        const std::vector<double> wcol = band_solve(ft, vcol);
+        std::vector<double> ucol(n, 0.0);
+        ucol[R[m]] = 1.0;
+        const std::vector<double> zcol = band_solve(f, ucol);
+        for (int j = 0; j < n; ++j) {
+            F.W[(size_t)j * 4 + m] = wcol[j];
+            F.Z[(size_t)j * 4 + m] = zcol[j];
+        }
+    }
+    double cap[16];
+    for (int p = 0; p < 4; ++p)
+        for (int q = 0; q < 4; ++q) {
+            double s = (p == q) ? 1.0 : 0.0;
+            for (int j = 0; j < n; ++j) s += Vt[(size_t)p * n + j] * F.Z[(size_t)j * 4 + q];
+            cap[p * 4 + q] = s;
+        }
+    F.ok = invert4(cap, F.S);
+    return F;
+}
+
+// Rows per lane of the warp-scan solver: the smallest power of two M with
+// 32 M >= n (n <= 1024).
+inline int warp_chunk(int n) {
+    int m = 1;
+    while (32 * m < n) m *= 2;
+    return m;
+}
+
+// Offsets (in elements) of the warp-scan tables inside one block.
+struct WarpLayout {
+    size_t fwd, bwd, W, Z, Pf, Pb, S, total;
+};
+
+inline WarpLayout warp_layout(int M) {
+    WarpLayout L;
+    size_t off = 0;
+    L.fwd = off; off += (size_t)M * 32 * 4;
+    L.bwd = off; off += (size_t)M * 32 * 2;
+    L.W = off;   off += (size_t)M * 32 * 4;
+    L.Z = off;   off += (size_t)M * 32 * 4;
+    L.Pf = off;  off += 5 * 32 * 4;
+    L.Pb = off;  off += 5 * 32 * 4;
+    L.S = off;   off += 16;
+    L.total = (off + 63) / 64 * 64;
+    return L;
+}
+
+// 2x2 row-major matrix product a * b.
+inline void mat2_mul(const double* a, const double* b, double* out) {
+    const double r0 = a[0] * b[0] + a[1] * b[2], r1 = a[0] * b[1] + a[1] * b[3];
+    const double r2 = a[2] * b[0] + a[3] * b[2], r3 = a[2] * b[1] + a[3] * b[3];
+    out[0] = r0; out[1] = r1; out[2] = r2; out[3] = r3;
+}
+
+// Tables of the warp-scan solver for chunk size M (see warp_line_solve):
+// per row (row j = lane*M + i stored at [i][lane]) the forward (l1, l2,
+// 1/u0, 0) and backward (u1/u0, u2/u0) coefficients and the Woodbury rows;
+// per lane and scan step s the transfer matrices of the lane span.  Rows
+// j >= n are padding with zero coefficients.
+inline std::vector<double> warp_tables(const LineFactors& F, int M) {
+    const WarpLayout L = warp_layout(M);
+    std::vector<double> t(L.total, 0.0);
+    const int n = F.n;
+    auto row = [&](int lane, int i) { return lane * M + i; };
+    for (int lane = 0; lane < 32; ++lane)
+        for (int i = 0; i < M; ++i) {
+            const int j = row(lane, i);
+            const size_t k = (size_t)i * 32 + lane;
+            if (j >= n) continue;
+            t[L.fwd + 4 * k + 0] = F.l1[j];
+            t[L.fwd + 4 * k + 1] = F.l2[j];
+            t[L.fwd + 4 * k + 2] = F.dinv[j];
+            t[L.bwd + 2 * k + 0] = F.u1s[j];
+            t[L.bwd + 2 * k + 1] = F.u2s[j];
+            if (F.periodic)
+                for (int m = 0; m < 4; ++m) {
+                    t[L.W + 4 * k + m] = F.W[(size_t)j * 4 + m];
+                    t[L.Z + 4 * k + m] = F.Z[(size_t)j * 4 + m];
+                }
+        }
+    // chunk transfer matrices: forward P_l = A_{b-1} ... A_a with
+    // A_j = [[-l1_j, -l2_j], [1, 0]]; backward Q_l = B_a ... B_{b-1} with
+    // B_j = [[-u1s_j, -u2s_j], [1, 0]]; padding rows are [[0,0],[1,0]].
+    std::vector<double> P(32 * 4), Q(32 * 4);
+    for (int lane = 0; lane < 32; ++lane) {
+        double p[4] = {1, 0, 0, 1}, q[4] = {1, 0, 0, 1};
+        for (int i = 0; i < M; ++i) {
+            const int j = row(lane, i);
+            const double A[4] = {j < n ? -F.l1[j] : 0.0, j < n ? -F.l2[j] : 0.0, 1.0, 0.0};
+            mat2_mul(A, p, p);  // p = A_j * p
+        }
+        for (int i = M - 1; i >= 0; --i) {
+            const int j = row(lane, i);
+            const double B[4] = {j < n ? -F.u1s[j] : 0.0, j < n ? -F.u2s[j] : 0.0, 1.0, 0.0};
+            mat2_mul(B, q, q);  // q = B_j * q, giving B_a ... B_{b-1}
+        }
+        for (int m = 0; m < 4; ++m) {
+            P[lane * 4 + m] = p[m];
+            Q[lane * 4 + m] = q[m];
+        }
+    }
+    for (int s = 0; s < 5; ++s) {
+        const int d = 1 << s;
+        for (int lane = 0; lane < 32; ++lane) {
+            // forward span over lanes lane-d+1 .. lane: P_lane ... P_{lane-d+1}
+            double sp[4] = {1, 0, 0, 1};
+            if (lane >= d)
+                for (int k = lane - d + 1; k <= lane; ++k) mat2_mul(&P[k * 4], sp, sp);
+            // backward span over lanes lane .. lane+d-1: Q_lane ... Q_{lane+d-1}
+            double sq[4] = {1, 0, 0, 1};
+            if (lane + d < 32)
+                for (int k = lane + d - 1; k >= lane; --k) mat2_mul(&Q[k * 4], sq, sq);
+            for (int m = 0; m < 4; ++m) {
+                t[L.Pf + ((size_t)s * 32 + lane) * 4 + m] = sp[m];
+                t[L.Pb + ((size_t)s * 32 + lane) * 4 + m] = sq[m];
+            }
+        }
+    }
+    if (F.periodic)
+        for (int m = 0; m < 16; ++m) t[L.S + m] = F.S[m];
+    return t;
+}
+
+}  // namespace chg
