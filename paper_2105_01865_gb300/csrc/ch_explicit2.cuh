@@ -1,0 +1,289 @@
+// Explicit right-hand side, two x-adjacent cells per thread (even nx).
+//
+// Same arithmetic as ch_explicit_rhs (arXiv 2105.01865, Sec. 3 and Eq. eq-re:
+// H^l = -div(uC)_WENO5 + M lap(psi'(C)), r = dt(gamma H^l + rho H^{l-1})
+// - alpha dt M sum_d A_d C), but every value is a pair belonging to the cells
+// (i, i+1) of one thread.  For float the pairs live in one 64-bit register and
+// map onto Blackwell's paired FP32 instructions (FADD2/FMUL2/FFMA2), so one
+// instruction advances the x-, y- or z-face reconstruction of both cells; the
+// global accesses become 8-byte (float2) or 16-byte (double2) vectors.
+#pragma once
+
+#include "ch_kernels.cuh"
+
+namespace chg {
+
+template <typename T>
+struct Pr;
+
+template <>
+struct Pr<float> {
+    float2 v;
+    __device__ __forceinline__ float x() const { return v.x; }
+    __device__ __forceinline__ float y() const { return v.y; }
+};
+
+template <>
+struct Pr<double> {
+    double2 v;
+    __device__ __forceinline__ double x() const { return v.x; }
+    __device__ __forceinline__ double y() const { return v.y; }
+};
+
+__device__ __forceinline__ Pr<float> mk(float a, float b) { return {make_float2(a, b)}; }
+__device__ __forceinline__ Pr<double> mk(double a, double b) { return {make_double2(a, b)}; }
+template <typename T>
+__device__ __forceinline__ Pr<T> sp(T a) { return mk(a, a); }
+
+__device__ __forceinline__ Pr<float> add(Pr<float> a, Pr<float> b) { return {__fadd2_rn(a.v, b.v)}; }
+__device__ __forceinline__ Pr<float> mul(Pr<float> a, Pr<float> b) { return {__fmul2_rn(a.v, b.v)}; }
+__device__ __forceinline__ Pr<float> fma2(Pr<float> a, Pr<float> b, Pr<float> c) { return {__ffma2_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ Pr<float> sub(Pr<float> a, Pr<float> b) {
+    return {__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)};  // a - b, one rounding
+}
+__device__ __forceinline__ Pr<float> divp(Pr<float> a, Pr<float> b) {
+    return mk(__fdividef(a.v.x, b.v.x), __fdividef(a.v.y, b.v.y));
+}
+
+__device__ __forceinline__ Pr<double> add(Pr<double> a, Pr<double> b) { return mk(a.v.x + b.v.x, a.v.y + b.v.y); }
+__device__ __forceinline__ Pr<double> mul(Pr<double> a, Pr<double> b) { return mk(a.v.x * b.v.x, a.v.y * b.v.y); }
+__device__ __forceinline__ Pr<double> fma2(Pr<double> a, Pr<double> b, Pr<double> c) {
+    return mk(fma(a.v.x, b.v.x, c.v.x), fma(a.v.y, b.v.y, c.v.y));
+}
+__device__ __forceinline__ Pr<double> sub(Pr<double> a, Pr<double> b) { return mk(a.v.x - b.v.x, a.v.y - b.v.y); }
+__device__ __forceinline__ Pr<double> divp(Pr<double> a, Pr<double> b) { return mk(a.v.x / b.v.x, a.v.y / b.v.y); }
+
+// aligned pair load/store (address of the first element of the pair)
+__device__ __forceinline__ Pr<float> ldp(const float* p) { return {*reinterpret_cast<const float2*>(p)}; }
+__device__ __forceinline__ Pr<double> ldp(const double* p) { return {*reinterpret_cast<const double2*>(p)}; }
+__device__ __forceinline__ void stp(float* p, Pr<float> a) { *reinterpret_cast<float2*>(p) = a.v; }
+__device__ __forceinline__ void stp(double* p, Pr<double> a) { *reinterpret_cast<double2*>(p) = a.v; }
+
+template <typename T>
+__device__ __forceinline__ Pr<T> psi_pp(Pr<T> c) {  // psi'(C) = C (C (C - 1.5) + 0.5)
+    return mul(c, fma2(c, sub(c, sp<T>(T(1.5))), sp<T>(T(0.5))));
+}
+
+// WENO5 (Jiang-Shu) face values of two faces at once; see weno5.
+template <typename T>
+__device__ __forceinline__ Pr<T> weno5p(Pr<T> v1, Pr<T> v2, Pr<T> v3, Pr<T> v4, Pr<T> v5, Pr<T> eps) {
+    const Pr<T> q0 = fma2(sp<T>(T(2)), v1, fma2(sp<T>(T(-7)), v2, mul(sp<T>(T(11)), v3)));
+    const Pr<T> q1 = fma2(sp<T>(T(2)), v4, fma2(sp<T>(T(5)), v3, mul(sp<T>(T(-1)), v2)));
+    const Pr<T> q2 = fma2(sp<T>(T(-1)), v5, fma2(sp<T>(T(5)), v4, mul(sp<T>(T(2)), v3)));
+    const Pr<T> d0 = fma2(sp<T>(T(-2)), v2, add(v1, v3));
+    const Pr<T> e0 = fma2(sp<T>(T(-4)), v2, fma2(sp<T>(T(3)), v3, v1));
+    const Pr<T> d1 = fma2(sp<T>(T(-2)), v3, add(v2, v4));
+    const Pr<T> e1 = sub(v2, v4);
+    const Pr<T> d2 = fma2(sp<T>(T(-2)), v4, add(v3, v5));
+    const Pr<T> e2 = fma2(sp<T>(T(-4)), v4, fma2(sp<T>(T(3)), v3, v5));
+    const Pr<T> c13 = sp<T>(T(13.0 / 12.0)), c14 = sp<T>(T(0.25));
+    const Pr<T> s0 = fma2(mul(c13, d0), d0, fma2(mul(c14, e0), e0, eps));
+    const Pr<T> s1 = fma2(mul(c13, d1), d1, fma2(mul(c14, e1), e1, eps));
+    const Pr<T> s2 = fma2(mul(c13, d2), d2, fma2(mul(c14, e2), e2, eps));
+    const Pr<T> t0 = mul(s0, s0), t1 = mul(s1, s1), t2 = mul(s2, s2);
+    const Pr<T> w0 = mul(sp<T>(T(0.1)), mul(t1, t2));
+    const Pr<T> w1 = mul(sp<T>(T(0.6)), mul(t0, t2));
+    const Pr<T> w2 = mul(sp<T>(T(0.3)), mul(t0, t1));
+    const Pr<T> num = fma2(w2, q2, fma2(w1, q1, mul(w0, q0)));
+    const Pr<T> den = mul(sp<T>(T(6)), add(add(w0, w1), w2));
+    return divp(num, den);
+}
+
+// Flux pair through two faces; m3..p2 are the cell pairs f-3 .. f+2.
+template <typename T>
+__device__ __forceinline__ Pr<T> face_flux_p(Pr<T> vel, Pr<T> m3, Pr<T> m2, Pr<T> m1, Pr<T> p0, Pr<T> p1, Pr<T> p2,
+                                             Pr<T> eps) {
+    const bool ux = vel.x() >= T(0), uy = vel.y() >= T(0);
+    const Pr<T> a1 = mk(ux ? m3.x() : p2.x(), uy ? m3.y() : p2.y());
+    const Pr<T> a2 = mk(ux ? m2.x() : p1.x(), uy ? m2.y() : p1.y());
+    const Pr<T> a3 = mk(ux ? m1.x() : p0.x(), uy ? m1.y() : p0.y());
+    const Pr<T> a4 = mk(ux ? p0.x() : m1.x(), uy ? p0.y() : m1.y());
+    const Pr<T> a5 = mk(ux ? p1.x() : m2.x(), uy ? p1.y() : m2.y());
+    return mul(vel, weno5p(a1, a2, a3, a4, a5, eps));
+}
+
+constexpr int kTX2 = 64;  // cells in x per CTA (two per thread)
+constexpr int kTZ2 = 8;   // z-planes marched per CTA
+constexpr int kHL2 = 4;   // left halo columns (even, so thread pairs stay 8/16-byte aligned)
+
+template <typename T, bool ADV>
+__global__ void __launch_bounds__(32 * kTY, sizeof(T) == 4 ? 3 : 2)
+ch_explicit_rhs2(const T* __restrict__ C, const T* __restrict__ u, const T* __restrict__ v,
+                 const T* __restrict__ w, const T* __restrict__ Hprev, T* __restrict__ Hout, T* __restrict__ r,
+                 RhsArgs<T> a) {
+    constexpr int PX = kTX2 + 2 * kHL2, PY = kTY + 2 * kHalo;  // 72 x 14
+    __shared__ __align__(16) T Cs[3][PY][PX];
+    __shared__ __align__(16) T Fx[ADV ? kTY : 1][kTX2 + 2];
+    __shared__ __align__(16) T Fy[ADV ? kTY + 1 : 1][kTX2];
+    __shared__ int gi_tab[PX], gj_tab[PY];
+
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    const int i0 = blockIdx.x * kTX2, j0 = blockIdx.y * kTY, k0 = blockIdx.z * kTZ2;
+    const int ia = i0 + 2 * tx, j = j0 + ty;   // this thread's cells: (ia, j) and (ia + 1, j)
+    const bool in_xy = (ia < a.nx) && (j < a.ny);
+    const int ic = min(ia, a.nx - 2), jc = min(j, a.ny - 1);
+    const int64_t plane = (int64_t)a.nx * a.ny;
+    const int64_t col = (int64_t)jc * a.nx + ic;
+    const Pr<T> eps = sp<T>(a.eps);
+    const int kend = min(k0 + kTZ2, a.nz);
+
+    if (tid < PX) gi_tab[tid] = bc_index(i0 + tid - kHL2, a.nx, a.bcx);
+    else if (tid < PX + PY) gj_tab[tid - PX] = bc_index(j0 + (tid - PX) - kHalo, a.ny, a.bcy);
+
+    // x-faces ia and ia+1 (lower faces of the two cells)
+    const bool wxa = (a.bcx == CH_NOFLUX) && (ia <= 0 || ia >= a.nx);
+    const bool wxb = (a.bcx == CH_NOFLUX) && (ia + 1 >= a.nx);
+    const int fxa = (a.bcx == CH_PERIODIC) ? bc_index(ia, a.nx, CH_PERIODIC) : min(ia, a.nx);
+    const int fxb = (a.bcx == CH_PERIODIC) ? bc_index(ia + 1, a.nx, CH_PERIODIC) : min(ia + 1, a.nx);
+    // y-face j (lower face of both cells)
+    const bool wy = (a.bcy == CH_NOFLUX) && (j <= 0 || j >= a.ny);
+    const int fy = (a.bcy == CH_PERIODIC) ? bc_index(j, a.ny, CH_PERIODIC) : min(j, a.ny);
+    // extra faces: y-face j0+8 for this thread's two columns (warp 0) and the
+    // x-face i0+64 of rows (2 tx, 2 tx + 1) (warp 1, lanes 0..3)
+    const int je = j0 + kTY;
+    const bool wye = (a.bcy == CH_NOFLUX) && (je >= a.ny);
+    const int fye = (a.bcy == CH_PERIODIC) ? bc_index(je, a.ny, CH_PERIODIC) : min(je, a.ny);
+    const int ie = i0 + kTX2;
+    const bool wxe = (a.bcx == CH_NOFLUX) && (ie >= a.nx);
+    const int fxe = (a.bcx == CH_PERIODIC) ? bc_index(ie, a.nx, CH_PERIODIC) : min(ie, a.nx);
+    const int jea = min(j0 + 2 * (tx & 3), a.ny - 1), jeb = min(j0 + 2 * (tx & 3) + 1, a.ny - 1);
+
+    // z-column queue of pairs: q[m] = C(ia..ia+1, jc, k - 2 + m)
+    Pr<T> q[6];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) q[m] = ldp(C + (int64_t)bc_near(k0 - 2 + m, a.nz, a.bcz) * plane + col);
+
+    Pr<T> fz_lo = sp<T>(T(0));
+    if (ADV) {
+        const bool wall = (a.bcz == CH_NOFLUX) && (k0 == 0);
+        if (!wall) {
+            const Pr<T> cm3 = ldp(C + (int64_t)bc_near(k0 - 3, a.nz, a.bcz) * plane + col);
+            const Pr<T> wv = ldp(w + (int64_t)k0 * plane + col);
+            fz_lo = face_flux_p(wv, cm3, q[0], q[1], q[2], q[3], q[4], eps);
+        }
+    }
+    __syncthreads();  // index tables ready
+
+    auto stage = [&](int kk, int b) {
+        const T* Ck = C + (int64_t)kk * plane;
+        for (int e = tid; e < PX * PY; e += 32 * kTY) {
+            const int row = e / PX, cc = e - row * PX;
+            cp_async_elem(&Cs[b][row][cc], Ck + (int64_t)gj_tab[row] * a.nx + gi_tab[cc]);
+        }
+        cp_async_commit();
+    };
+    stage(k0, 0);
+    for (int k = k0, buf = 0; k < kend; ++k, buf = (buf == 2 ? 0 : buf + 1)) {
+        if (k + 1 < kend) {
+            stage(k + 1, buf == 2 ? 0 : buf + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        // per-thread global inputs of this plane (issued before the barrier)
+        const Pr<T> qnext = ldp(C + (int64_t)bc_near(k + 4, a.nz, a.bcz) * plane + col);
+        const int64_t kp = (int64_t)k * a.ny;
+        T uxa = T(0), uxb = T(0), uxe_a = T(0), uxe_b = T(0);
+        Pr<T> vy = sp<T>(T(0)), vye = sp<T>(T(0)), wz = sp<T>(T(0)), hp = sp<T>(T(0));
+        const bool zwall = (a.bcz == CH_NOFLUX) && (k + 1 >= a.nz);
+        if (ADV) {
+            uxa = wxa ? T(0) : u[(kp + jc) * a.nfx + fxa];
+            uxb = wxb ? T(0) : u[(kp + jc) * a.nfx + fxb];
+            if (!wy) vy = ldp(v + ((int64_t)k * a.nfy + fy) * a.nx + ic);
+            if (ty == 0 && !wye) vye = ldp(v + ((int64_t)k * a.nfy + fye) * a.nx + ic);
+            if (ty == 1 && tx < 4 && !wxe) {
+                uxe_a = u[(kp + jea) * a.nfx + fxe];
+                uxe_b = u[(kp + jeb) * a.nfx + fxe];
+            }
+            if (!zwall) wz = ldp(w + (int64_t)((k + 1 < a.nz) ? k + 1 : 0) * plane + col);
+        }
+        if (a.has_prev && in_xy) hp = ldp(Hprev + (int64_t)k * plane + (int64_t)j * a.nx + ia);
+        __syncthreads();
+
+        const T(*P)[PX] = Cs[buf];
+        const int cy = ty + kHalo, cx = 2 * tx + kHL2;  // smem position of cell ia
+        // row of 7 cells ia-3 .. ia+3 and the y-column pairs rows j-3 .. j+2
+        const T s1 = P[cy][cx - 3], s2 = P[cy][cx - 2], s3 = P[cy][cx - 1], s4 = P[cy][cx], s5 = P[cy][cx + 1],
+                s6 = P[cy][cx + 2], s7 = P[cy][cx + 3];
+        const Pr<T> ym3 = ldp(&P[cy - 3][cx]), ym2 = ldp(&P[cy - 2][cx]), ym1 = ldp(&P[cy - 1][cx]);
+        const Pr<T> c0 = mk(s4, s5);
+        const Pr<T> yp1 = ldp(&P[cy + 1][cx]), yp2 = ldp(&P[cy + 2][cx]);
+        Pr<T> fz_up = sp<T>(T(0));
+        if (ADV) {
+            // x: lower faces of the two cells (faces ia, ia+1)
+            const Pr<T> fx = face_flux_p(mk(uxa, uxb), mk(s1, s2), mk(s2, s3), mk(s3, s4), mk(s4, s5), mk(s5, s6),
+                                         mk(s6, s7), eps);
+            Fx[ty][2 * tx] = wxa ? T(0) : fx.x();
+            Fx[ty][2 * tx + 1] = wxb ? T(0) : fx.y();
+            // y: lower faces (face j) of the two cells
+            Pr<T> fyp = sp<T>(T(0));
+            if (!wy) fyp = face_flux_p(vy, ym3, ym2, ym1, c0, yp1, yp2, eps);
+            stp(&Fy[ty][2 * tx], fyp);
+            // extra faces
+            if (ty == 0) {
+                Pr<T> f = sp<T>(T(0));
+                if (!wye) {
+                    const int yy = kTY + kHalo;
+                    f = face_flux_p(vye, ldp(&P[yy - 3][cx]), ldp(&P[yy - 2][cx]), ldp(&P[yy - 1][cx]),
+                                    ldp(&P[yy][cx]), ldp(&P[yy + 1][cx]), ldp(&P[yy + 2][cx]), eps);
+                }
+                stp(&Fy[kTY][2 * tx], f);
+            }
+            if (ty == 1 && tx < 4) {
+                // x-face i0+64 of rows ra = 2(tx) and rb = 2(tx)+1 of the tile
+                const int ra = 2 * tx + kHalo, rb = ra + 1, xx = kTX2 + kHL2;
+                Pr<T> f = sp<T>(T(0));
+                if (!wxe) {
+                    f = face_flux_p(mk(uxe_a, uxe_b), mk(P[ra][xx - 3], P[rb][xx - 3]), mk(P[ra][xx - 2], P[rb][xx - 2]),
+                                    mk(P[ra][xx - 1], P[rb][xx - 1]), mk(P[ra][xx], P[rb][xx]),
+                                    mk(P[ra][xx + 1], P[rb][xx + 1]), mk(P[ra][xx + 2], P[rb][xx + 2]), eps);
+                }
+                Fx[2 * tx][kTX2] = f.x();
+                Fx[2 * tx + 1][kTX2] = f.y();
+            }
+            // z: upper face k+1 of the two cells
+            if (!zwall) fz_up = face_flux_p(wz, q[0], q[1], q[2], q[3], q[4], q[5], eps);
+            __syncthreads();
+        }
+
+        // M lap(psi'(C)), 7-point central (Sec. 3); neighbour differences are
+        // formed first, so FP32 keeps the accuracy of the small differences
+        const Pr<T> xl = mk(s3, s4), xr = mk(s5, s6);
+        const Pr<T> pc = psi_pp(c0);
+        const Pr<T> lap = mul(add(add(add(sub(psi_pp(xl), pc), sub(psi_pp(xr), pc)),
+                                      add(sub(psi_pp(ym1), pc), sub(psi_pp(yp1), pc))),
+                                  add(sub(psi_pp(q[1]), pc), sub(psi_pp(q[3]), pc))),
+                              sp<T>(a.inv_h2));
+        // [1,-4,6,-4,1] sums of A_x + A_y + A_z (Eq. eq-a3d) as differences of
+        // second differences: D2(i-1) - 2 D2(i) + D2(i+1)
+        auto fourth = [&](Pr<T> m2, Pr<T> m1, Pr<T> p1, Pr<T> p2) {
+            const Pr<T> da = sub(m1, c0), db = sub(p1, c0);
+            const Pr<T> dm = sub(sub(m2, m1), da), dp = sub(sub(p2, p1), db);
+            return fma2(sp<T>(T(-2)), add(da, db), add(dm, dp));
+        };
+        const Pr<T> astar = add(add(fourth(mk(s2, s3), xl, xr, mk(s6, s7)), fourth(ym2, ym1, yp1, yp2)),
+                                fourth(q[0], q[1], q[3], q[4]));
+
+        Pr<T> H = mul(sp<T>(a.mob), lap);
+        if (ADV) {
+            const T f0 = Fx[ty][2 * tx], f1 = Fx[ty][2 * tx + 1], f2 = Fx[ty][2 * tx + 2];
+            const Pr<T> dxf = mk(f1 - f0, f2 - f1);
+            const Pr<T> dyf = sub(ldp(&Fy[ty + 1][2 * tx]), ldp(&Fy[ty][2 * tx]));
+            const Pr<T> div = add(add(dxf, dyf), sub(fz_up, fz_lo));
+            H = fma2(sp<T>(-a.inv_h), div, H);
+        }
+        if (in_xy) {
+            const int64_t idx = (int64_t)k * plane + (int64_t)j * a.nx + ia;
+            Pr<T> rhs = fma2(sp<T>(-a.impl), astar, mul(sp<T>(a.dtg), H));
+            if (a.has_prev) rhs = fma2(sp<T>(a.dtr), hp, rhs);
+            stp(Hout + idx, H);
+            stp(r + idx, rhs);
+        }
+#pragma unroll
+        for (int m = 0; m < 5; ++m) q[m] = q[m + 1];
+        q[5] = qnext;
+        fz_lo = fz_up;
+    }
+}
+
+}  // namespace chg

@@ -256,16 +256,23 @@ ch_explicit_rhs(const T* __restrict__ C, const T* __restrict__ u, const T* __res
             __syncthreads();
         }
 
-        // M lap(psi'(C)), 7-point central (Sec. 3)
+        // M lap(psi'(C)), 7-point central (Sec. 3); neighbour differences are
+        // formed first, so FP32 keeps the accuracy of the small differences
         const T c0 = Cs[buf][cy][cx];
-        const T lap = (psi_p(Cs[buf][cy][cx - 1]) + psi_p(Cs[buf][cy][cx + 1]) + psi_p(Cs[buf][cy - 1][cx]) +
-                       psi_p(Cs[buf][cy + 1][cx]) + psi_p(q[1]) + psi_p(q[3]) - T(6) * psi_p(c0)) *
+        const T pc = psi_p(c0);
+        const T lap = (((psi_p(Cs[buf][cy][cx - 1]) - pc) + (psi_p(Cs[buf][cy][cx + 1]) - pc)) +
+                       ((psi_p(Cs[buf][cy - 1][cx]) - pc) + (psi_p(Cs[buf][cy + 1][cx]) - pc)) +
+                       ((psi_p(q[1]) - pc) + (psi_p(q[3]) - pc))) *
                       a.inv_h2;
-        // raw [1,-4,6,-4,1] sums of A_x + A_y + A_z (Eq. eq-a3d)
-        const T ax = Cs[buf][cy][cx - 2] + Cs[buf][cy][cx + 2] - T(4) * (Cs[buf][cy][cx - 1] + Cs[buf][cy][cx + 1]);
-        const T ay = Cs[buf][cy - 2][cx] + Cs[buf][cy + 2][cx] - T(4) * (Cs[buf][cy - 1][cx] + Cs[buf][cy + 1][cx]);
-        const T az = q[0] + q[4] - T(4) * (q[1] + q[3]);
-        const T astar = ax + ay + az + T(18) * c0;
+        // [1,-4,6,-4,1] sums of A_x + A_y + A_z (Eq. eq-a3d) as differences of
+        // second differences: D2(i-1) - 2 D2(i) + D2(i+1)
+        auto fourth = [&](T m2, T m1, T p1, T p2) {
+            const T da = m1 - c0, db = p1 - c0;
+            return ((m2 - m1) - da) + ((p2 - p1) - db) - T(2) * (da + db);
+        };
+        const T astar = fourth(Cs[buf][cy][cx - 2], Cs[buf][cy][cx - 1], Cs[buf][cy][cx + 1], Cs[buf][cy][cx + 2]) +
+                        fourth(Cs[buf][cy - 2][cx], Cs[buf][cy - 1][cx], Cs[buf][cy + 1][cx], Cs[buf][cy + 2][cx]) +
+                        fourth(q[0], q[1], q[3], q[4]);
 
         T H = a.mob * lap;
         if (ADV) {

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "ch_internal.h"
+#include "ch_explicit2.cuh"
 #include "ch_kernels.cuh"
 #include "line_tables.h"
 
@@ -198,14 +199,25 @@ int launch_substep(ch_handle* h, int l, cudaEvent_t* ev = nullptr) {
     T* Hout = (T*)h->H[l & 1];
     const T* Hprev = (const T*)h->H[(l + 1) & 1];
     T* r = (T*)h->r;
-    dim3 grid((nx + kTX - 1) / kTX, (ny + kTY - 1) / kTY, (nz + kTZ - 1) / kTZ);
-    dim3 block(kTX, kTY);
+    const T* u = p.advect ? (const T*)h->vel[0] : nullptr;
+    const T* v = p.advect ? (const T*)h->vel[1] : nullptr;
+    const T* w = p.advect ? (const T*)h->vel[2] : nullptr;
     if (ev) CHG_CUDA(h, cudaEventRecord(ev[0], h->stream));
-    if (p.advect)
-        ch_explicit_rhs<T, true><<<grid, block, 0, h->stream>>>(C, (const T*)h->vel[0], (const T*)h->vel[1],
-                                                                (const T*)h->vel[2], Hprev, Hout, r, a);
-    else
-        ch_explicit_rhs<T, false><<<grid, block, 0, h->stream>>>(C, nullptr, nullptr, nullptr, Hprev, Hout, r, a);
+    if (nx % 2 == 0) {  // two cells per thread (paired FP32 arithmetic)
+        dim3 grid((nx + kTX2 - 1) / kTX2, (ny + kTY - 1) / kTY, (nz + kTZ2 - 1) / kTZ2);
+        dim3 block(32, kTY);
+        if (p.advect)
+            ch_explicit_rhs2<T, true><<<grid, block, 0, h->stream>>>(C, u, v, w, Hprev, Hout, r, a);
+        else
+            ch_explicit_rhs2<T, false><<<grid, block, 0, h->stream>>>(C, u, v, w, Hprev, Hout, r, a);
+    } else {
+        dim3 grid((nx + kTX - 1) / kTX, (ny + kTY - 1) / kTY, (nz + kTZ - 1) / kTZ);
+        dim3 block(kTX, kTY);
+        if (p.advect)
+            ch_explicit_rhs<T, true><<<grid, block, 0, h->stream>>>(C, u, v, w, Hprev, Hout, r, a);
+        else
+            ch_explicit_rhs<T, false><<<grid, block, 0, h->stream>>>(C, u, v, w, Hprev, Hout, r, a);
+    }
     CHG_CUDA(h, cudaGetLastError());
     if (ev) CHG_CUDA(h, cudaEventRecord(ev[1], h->stream));
 

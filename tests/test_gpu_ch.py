@@ -66,6 +66,10 @@ def test_fp64_single_drop_box_100_steps():
     ((37, 11, 40), (co.PERIODIC, co.NOFLUX, co.PERIODIC)),   # several z chunks, ragged tail
     ((6, 5, 7), (co.PERIODIC, co.PERIODIC, co.PERIODIC)),    # near the minimum size
     ((5, 6, 5), (co.NOFLUX, co.NOFLUX, co.NOFLUX)),          # minimum size, all walls
+    # even nx: the two-cells-per-thread kernel
+    ((9, 17, 34), (co.NOFLUX, co.PERIODIC, co.NOFLUX)),      # x walls (odd face count), ragged tiles
+    ((20, 10, 70), (co.PERIODIC, co.PERIODIC, co.NOFLUX)),   # two x tiles, ragged tail
+    ((6, 5, 6), (co.PERIODIC, co.NOFLUX, co.PERIODIC)),      # minimum even size
 ])
 def test_fp64_advected_ragged(shape, bc):
     h = 1.0 / 16
