@@ -162,6 +162,69 @@ int ch_launches_per_step(const ch_handle* h);
  * Errors: CH_EINVAL, CH_ECUDA. */
 int ch_profile_step(ch_handle* h, int64_t nsteps, double* ms_out);
 
+/* ---------------------------------------------------------------------------
+ * Batched form: many independent boxes of uneven sizes and parameters
+ * (each box is the Sec. 3 step of its own ch_params) advanced together.  The
+ * paper advances one box; batching is this library's addition.
+ * Restrictions: precision CH_F32, advect = 0, no coarse mesh, nx even,
+ * 6 <= nx and 5 <= ny, nz, every size <= 256.  Same conventions as above.
+ * ------------------------------------------------------------------------- */
+typedef struct ch_batch ch_batch;
+
+/* Workspace bytes for the boxes (3 fields per box, 256-byte aligned); 0 if
+ * any box violates the restrictions. */
+size_t ch_batch_workspace_bytes(const ch_params* boxes, int nbox);
+
+/* Create a batch.  C[i]: device array [nz][ny][nx] of box i (16-byte
+ * aligned), advanced in place.  work: >= ch_batch_workspace_bytes bytes,
+ * 256-byte aligned.  Builds every box's line-solve tables.  Default schedule:
+ * one persistent cooperative launch per step (if the device supports it).
+ * Errors: CH_EINVAL, CH_ENOMEM, CH_ECUDA. */
+int ch_batch_create(const ch_params* boxes, int nbox, void* const* C, void* work, size_t work_bytes, void* stream,
+                    ch_batch** out);
+
+/* nsteps full RK3 steps of every box.  Persistent schedule: one cooperative
+ * launch per step, 12 phases separated by grid barriers whose wait is
+ * bounded in time; an expired wait makes the kernel return early and the
+ * next ch_batch_sync / ch_batch_mass report CH_ETIMEOUT.  Phased schedule:
+ * 12 launches per step.  Both are captured once in a CUDA graph on a user
+ * stream.  Asynchronous. */
+int ch_batch_step(ch_batch* b, int64_t nsteps);
+
+/* FP64 mass h^3 sum C of every box into the host array out[nbox]; waits. */
+int ch_batch_mass(ch_batch* b, double* out);
+
+/* Wait for the stream; report (then clear) a barrier timeout (CH_ETIMEOUT)
+ * or a non-finite value (CH_ENONFINITE). */
+int ch_batch_sync(ch_batch* b);
+
+/* Schedule: mode 0 = persistent, 1 = phased; CTAs per SM (capped by
+ * occupancy); z extent of the explicit tiles; lpt = 1 orders each phase's
+ * work items by decreasing cost. */
+int ch_batch_set_schedule(ch_batch* b, int mode, int blocks_per_sm, int zchunk, int lpt);
+
+/* Current schedule as {mode, blocks_per_sm, zchunk, lpt}. */
+int ch_batch_get_schedule(const ch_batch* b, int* out4);
+
+/* Autotuner: time every schedule candidate over steps_per_trial steps (the
+ * boxes' fields are saved and restored), keep the fastest, and write one
+ * line per candidate plus the choice into report (if not NULL). */
+int ch_batch_autotune(ch_batch* b, int steps_per_trial, char* report, size_t report_len);
+
+/* Failure-detection hook: the barrier wait limit in nanoseconds (>= 1000)
+ * and, with poison = 1, a barrier that expects one CTA more than launched, so
+ * that every wait expires (used to test the timeout path). */
+int ch_batch_set_barrier_limit(ch_batch* b, int64_t limit_ns, int poison);
+
+/* Kernel launches one ch_batch_step(b, 1) enqueues. */
+int ch_batch_launches_per_step(const ch_batch* b);
+
+/* Release the batch's tables (not the fields or the workspace). */
+int ch_batch_free(ch_batch* b);
+
+/* Message of the last error on this batch ("" if none). */
+const char* ch_batch_last_error(const ch_batch* b);
+
 /* Mass h^3 * sum(C) without any device allocation; the paper has no
  * counterpart (it is an interface for callers that cannot call cudaMalloc,
  * e.g. an application that owns the device memory budget through its own

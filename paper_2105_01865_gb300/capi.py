@@ -64,6 +64,19 @@ SIGNATURES = [
     ("ch_profile_step", ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]),
     ("ch_mass_noalloc", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
                                         ctypes.c_int, _P, _P]),
+    ("ch_batch_workspace_bytes", ctypes.c_size_t, [ctypes.POINTER(ch_params), ctypes.c_int]),
+    ("ch_batch_create", ctypes.c_int, [ctypes.POINTER(ch_params), ctypes.c_int, ctypes.POINTER(_P), _P, ctypes.c_size_t,
+                                       _P, ctypes.POINTER(_P)]),
+    ("ch_batch_step", ctypes.c_int, [_P, ctypes.c_int64]),
+    ("ch_batch_mass", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    ("ch_batch_sync", ctypes.c_int, [_P]),
+    ("ch_batch_set_schedule", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    ("ch_batch_get_schedule", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    ("ch_batch_autotune", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t]),
+    ("ch_batch_set_barrier_limit", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int]),
+    ("ch_batch_launches_per_step", ctypes.c_int, [_P]),
+    ("ch_batch_free", ctypes.c_int, [_P]),
+    ("ch_batch_last_error", ctypes.c_char_p, [_P]),
     ("ch_error_string", ctypes.c_char_p, [ctypes.c_int]),
     ("ch_last_error", ctypes.c_char_p, [_P]),
 ]
@@ -199,6 +212,75 @@ def ch_mass_noalloc(C, h, out, stream):
     st = load().ch_mass_noalloc(_ptr(C), nx, ny, nz, h, prec, _ptr(out), ctypes.c_void_p(stream.cuda_stream))
     if st != CH_OK:
         raise CHError(st, f"ch_mass_noalloc: {ch_error_string(st)} (grid limit 268435456 cells)")
+
+
+def _bcheck(status, batch, what):
+    if status != CH_OK:
+        lib = load()
+        msg = lib.ch_batch_last_error(batch).decode() if batch else ""
+        raise CHError(status, f"{what}: {lib.ch_error_string(status).decode()} {msg}".strip())
+
+
+def ch_batch_workspace_bytes(params_list):
+    arr = (ch_params * len(params_list))(*params_list)
+    return int(load().ch_batch_workspace_bytes(arr, len(params_list)))
+
+
+def ch_batch_create(params_list, C_list, work, stream):
+    lib = load()
+    arr = (ch_params * len(params_list))(*params_list)
+    ptrs = (_P * len(C_list))(*[t.data_ptr() for t in C_list])
+    out = ctypes.c_void_p()
+    st = lib.ch_batch_create(arr, len(params_list), ptrs, _ptr(work), work.numel() * work.element_size(),
+                             ctypes.c_void_p(stream.cuda_stream), ctypes.byref(out))
+    _bcheck(st, None, "ch_batch_create")
+    return out
+
+
+def ch_batch_step(batch, nsteps):
+    _bcheck(load().ch_batch_step(batch, nsteps), batch, "ch_batch_step")
+
+
+def ch_batch_mass(batch, nbox):
+    out = (ctypes.c_double * nbox)()
+    _bcheck(load().ch_batch_mass(batch, out), batch, "ch_batch_mass")
+    return list(out)
+
+
+def ch_batch_sync(batch):
+    _bcheck(load().ch_batch_sync(batch), batch, "ch_batch_sync")
+
+
+def ch_batch_set_schedule(batch, mode, blocks_per_sm, zchunk, lpt):
+    _bcheck(load().ch_batch_set_schedule(batch, mode, blocks_per_sm, zchunk, lpt), batch, "ch_batch_set_schedule")
+
+
+def ch_batch_get_schedule(batch):
+    out = (ctypes.c_int * 4)()
+    _bcheck(load().ch_batch_get_schedule(batch, out), batch, "ch_batch_get_schedule")
+    return tuple(out)
+
+
+def ch_batch_autotune(batch, steps_per_trial):
+    buf = ctypes.create_string_buffer(8192)
+    _bcheck(load().ch_batch_autotune(batch, steps_per_trial, buf, len(buf)), batch, "ch_batch_autotune")
+    return buf.value.decode()
+
+
+def ch_batch_set_barrier_limit(batch, limit_ns, poison):
+    _bcheck(load().ch_batch_set_barrier_limit(batch, limit_ns, poison), batch, "ch_batch_set_barrier_limit")
+
+
+def ch_batch_launches_per_step(batch):
+    return int(load().ch_batch_launches_per_step(batch))
+
+
+def ch_batch_free(batch):
+    _bcheck(load().ch_batch_free(batch), None, "ch_batch_free")
+
+
+def ch_batch_last_error(batch):
+    return load().ch_batch_last_error(batch).decode()
 
 
 def ch_error_string(status):

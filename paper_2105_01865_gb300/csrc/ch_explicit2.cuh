@@ -106,27 +106,33 @@ constexpr int kTX2 = 64;  // cells in x per CTA (two per thread)
 constexpr int kTZ2 = 8;   // z-planes marched per CTA
 constexpr int kHL2 = 4;   // left halo columns (even, so thread pairs stay 8/16-byte aligned)
 
+// One 64 x 8 x zchunk tile (tile coordinates bx, by, bz) computed by the 256
+// threads of a CTA; called by the standalone kernel below and by the batched
+// persistent kernel.
 template <typename T, bool ADV>
-__global__ void __launch_bounds__(32 * kTY, sizeof(T) == 4 ? 3 : 2)
-ch_explicit_rhs2(const T* __restrict__ C, const T* __restrict__ u, const T* __restrict__ v,
-                 const T* __restrict__ w, const T* __restrict__ Hprev, T* __restrict__ Hout, T* __restrict__ r,
-                 RhsArgs<T> a) {
+// Data pointers carry no __restrict__ here: the batched persistent kernel
+// writes these arrays in one phase and reads them in the next, so their loads
+// must not go through the non-coherent read-only path.
+__device__ __forceinline__ void explicit_tile2(const T* C, const T* u, const T* v, const T* w, const T* Hprev,
+                                               T* Hout, T* r, const RhsArgs<T>& a, int bx, int by, int bz,
+                                               int zchunk) {
     constexpr int PX = kTX2 + 2 * kHL2, PY = kTY + 2 * kHalo;  // 72 x 14
     __shared__ __align__(16) T Cs[3][PY][PX];
     __shared__ __align__(16) T Fx[ADV ? kTY : 1][kTX2 + 2];
     __shared__ __align__(16) T Fy[ADV ? kTY + 1 : 1][kTX2];
     __shared__ int gi_tab[PX], gj_tab[PY];
 
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-    const int i0 = blockIdx.x * kTX2, j0 = blockIdx.y * kTY, k0 = blockIdx.z * kTZ2;
+    const int tid = threadIdx.x + threadIdx.y * 32, tx = tid & 31, ty = tid >> 5;
+    const int i0 = bx * kTX2, j0 = by * kTY, k0 = bz * zchunk;
     const int ia = i0 + 2 * tx, j = j0 + ty;   // this thread's cells: (ia, j) and (ia + 1, j)
     const bool in_xy = (ia < a.nx) && (j < a.ny);
     const int ic = min(ia, a.nx - 2), jc = min(j, a.ny - 1);
     const int64_t plane = (int64_t)a.nx * a.ny;
     const int64_t col = (int64_t)jc * a.nx + ic;
     const Pr<T> eps = sp<T>(a.eps);
-    const int kend = min(k0 + kTZ2, a.nz);
+    const int kend = min(k0 + zchunk, a.nz);
 
+    __syncthreads();  // the tables and buffers may still be read by a previous tile of this CTA
     if (tid < PX) gi_tab[tid] = bc_index(i0 + tid - kHL2, a.nx, a.bcx);
     else if (tid < PX + PY) gj_tab[tid - PX] = bc_index(j0 + (tid - PX) - kHalo, a.ny, a.bcy);
 
@@ -284,6 +290,14 @@ ch_explicit_rhs2(const T* __restrict__ C, const T* __restrict__ u, const T* __re
         q[5] = qnext;
         fz_lo = fz_up;
     }
+}
+
+template <typename T, bool ADV>
+__global__ void __launch_bounds__(32 * kTY, sizeof(T) == 4 ? 3 : 2)
+ch_explicit_rhs2(const T* __restrict__ C, const T* __restrict__ u, const T* __restrict__ v,
+                 const T* __restrict__ w, const T* __restrict__ Hprev, T* __restrict__ Hout, T* __restrict__ r,
+                 RhsArgs<T> a) {
+    explicit_tile2<T, ADV>(C, u, v, w, Hprev, Hout, r, a, blockIdx.x, blockIdx.y, blockIdx.z, kTZ2);
 }
 
 }  // namespace chg

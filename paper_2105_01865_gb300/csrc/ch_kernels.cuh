@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/ch.h"
+
 namespace chg {
 
 constexpr int kTX = 32;   // explicit-kernel tile, x (one warp)
@@ -455,11 +457,8 @@ __device__ __forceinline__ void warp_line_solve(T (&v)[M], const WCoef<T>& cf, i
 // x-lines (contiguous): one warp per line, lane chunks read and written
 // directly (16-byte vectors when the line and chunk are aligned).
 template <typename T, int M>
-__global__ void __launch_bounds__(256)
-ch_solve_x(T* __restrict__ a, int64_t nlines, int nx, WCoef<T> cf) {
+__device__ __forceinline__ void solve_x_line(T* a, int64_t line, int nx, const WCoef<T>& cf) {
     const int lane = threadIdx.x & 31;
-    const int64_t line = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (line >= nlines) return;  // whole warp
     T* p = a + line * nx;
     const int j0 = lane * M;
     T v[M];
@@ -501,6 +500,14 @@ ch_solve_x(T* __restrict__ a, int64_t nlines, int nx, WCoef<T> cf) {
     }
 }
 
+template <typename T, int M>
+__global__ void __launch_bounds__(256)
+ch_solve_x(T* __restrict__ a, int64_t nlines, int nx, WCoef<T> cf) {
+    const int64_t line = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (line >= nlines) return;  // whole warp
+    solve_x_line<T, M>(a, line, nx, cf);
+}
+
 // y- or z-lines (strided).  A CTA of 16 warps owns 32 consecutive x of one
 // outer position: the [n][32] tile is staged through shared memory with
 // coalesced 32-wide rows; element (row j, column c) sits at j*32 + (c ^ (j/M)
@@ -516,22 +523,22 @@ struct YZShape {
     static constexpr int kMinBlocks = kLong ? 1 : 2;
 };
 
-template <typename T, int M, bool UPDATE>
-__global__ void __launch_bounds__(YZShape<T, M>::kWarps * 32, YZShape<T, M>::kMinBlocks)
-ch_solve_yz(T* __restrict__ a, T* __restrict__ Cf, int nx, int64_t outer_stride, int64_t line_stride,
-            WCoef<T> cf, unsigned int* status) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* s = reinterpret_cast<T*>(smem_raw);
-    constexpr int kYZWarps = YZShape<T, M>::kWarps;
+// One [n][32] tile (tile index = x-block + xblocks * outer) solved by the
+// kYZWarps warps of a CTA; s is the CTA's shared tile of 32 M x 32 values.
+template <typename T, int M, bool UPDATE, int kYZWarps>
+__device__ __forceinline__ void solve_yz_tile(T* a, T* Cf, int nx, int64_t outer_stride,
+                                              int64_t line_stride, const WCoef<T>& cf, unsigned int* status,
+                                              int64_t tile, T* s) {
     const int n = cf.n;
     const int xblocks = (nx + 31) >> 5;
-    const int xb = blockIdx.x % xblocks;
-    const int64_t outer = blockIdx.x / xblocks;
+    const int xb = (int)(tile % xblocks);
+    const int64_t outer = tile / xblocks;
     const int i0 = xb * 32;
     const int nl = min(32, nx - i0);
     const int64_t base = outer * outer_stride + i0;
-    const int tid = threadIdx.x, c = tid & 31, r0 = tid >> 5;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x, c = tid & 31, r0 = tid >> 5;
     auto slot = [&](int j, int col) { return j * 32 + (col ^ ((j / M) & 31)); };
+    __syncthreads();  // the tile may still be read by a previous item of this CTA
     // stage rows asynchronously (zero padding past n and past the ragged x edge)
 #pragma unroll
     for (int j = r0; j < 32 * M; j += kYZWarps) {
@@ -570,6 +577,15 @@ ch_solve_yz(T* __restrict__ a, T* __restrict__ Cf, int nx, int64_t outer_stride,
         }
     }
     if (UPDATE && bad) atomicOr(status, 1u);
+}
+
+template <typename T, int M, bool UPDATE>
+__global__ void __launch_bounds__(YZShape<T, M>::kWarps * 32, YZShape<T, M>::kMinBlocks)
+ch_solve_yz(T* __restrict__ a, T* __restrict__ Cf, int nx, int64_t outer_stride, int64_t line_stride,
+            WCoef<T> cf, unsigned int* status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    solve_yz_tile<T, M, UPDATE, YZShape<T, M>::kWarps>(a, Cf, nx, outer_stride, line_stride, cf, status, blockIdx.x,
+                                                        reinterpret_cast<T*>(smem_raw));
 }
 
 // ---------------------------------------------------------------------------
@@ -633,7 +649,7 @@ ch_reduce_energy(const T* __restrict__ C, int nx, int ny, int nz, int bcx, int b
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
-__global__ void __launch_bounds__(kRedThreads)
+static __global__ void __launch_bounds__(kRedThreads)
 ch_reduce_finish(const double* __restrict__ partials, int nb, double scale, double* out) {
     double acc = 0.0;
     for (int b = threadIdx.x; b < nb; b += kRedThreads) acc += partials[b];

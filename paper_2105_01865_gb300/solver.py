@@ -110,3 +110,65 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Many independent FP32 boxes (u = 0) advanced together by libch.so's
+    batched form.  boxes: list of dicts with shape, h, bc, cn, pe, dt, C."""
+
+    def __init__(self, boxes, w=4.0, weno_eps=1e-6, device="cuda:0", stream=None):
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        self.params = [capi.make_params(b["shape"], b["h"], b["bc"], b["cn"], b["pe"], b["dt"], capi.CH_F32, w,
+                                        weno_eps, False) for b in boxes]
+        nbytes = capi.ch_batch_workspace_bytes(self.params)
+        if nbytes == 0:
+            raise capi.CHError(capi.CH_EINVAL, "invalid batch parameters")
+        self.C = [torch.as_tensor(np.asarray(b["C"]), dtype=torch.float32).to(self.device).contiguous()
+                  for b in boxes]
+        self.work = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.device(self.device):
+            self.handle = capi.ch_batch_create(self.params, self.C, self.work, self.stream)
+
+    def step(self, nsteps=1):
+        capi.ch_batch_step(self.handle, nsteps)
+
+    def mass(self):
+        return capi.ch_batch_mass(self.handle, len(self.C))
+
+    def sync(self):
+        capi.ch_batch_sync(self.handle)
+
+    def set_schedule(self, mode, blocks_per_sm, zchunk, lpt):
+        capi.ch_batch_set_schedule(self.handle, mode, blocks_per_sm, zchunk, lpt)
+
+    def schedule(self):
+        return capi.ch_batch_get_schedule(self.handle)
+
+    def autotune(self, steps_per_trial=3):
+        return capi.ch_batch_autotune(self.handle, steps_per_trial)
+
+    def fields(self):
+        self.stream.synchronize()
+        return [c.cpu().numpy().astype(np.float64) for c in self.C]
+
+    def set_fields(self, arrays):
+        for c, a in zip(self.C, arrays):
+            c.copy_(torch.as_tensor(np.asarray(a), dtype=torch.float32))
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+
+    def launches_per_step(self):
+        return capi.ch_batch_launches_per_step(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            self.stream.synchronize()
+            capi.ch_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
