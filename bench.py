@@ -24,6 +24,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -181,6 +183,63 @@ def measured_peak_hbm():
     return 6800.0, "fallback"
 
 
+def kernel_source_sha():
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2105_01865_gb300", "csrc")
+    hsh = hashlib.sha256()
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            hsh.update(name.encode() + fh.read())
+    return hsh.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per launch (ncu dram__bytes_read + write) recorded in
+    profiles/ncu_traffic.json, only if it was taken on the current kernels."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+    except (OSError, ValueError):
+        return {}
+    if rec.get("source_sha") != kernel_source_sha():
+        return {}
+    return rec.get("bytes_per_launch", {})
+
+
+def batched_leg(args, dev, flush):
+    """The batched form on 64 uneven periodic boxes (32^3 .. 128^3), u = 0."""
+    import torch
+    from paper_2105_01865_gb300 import inputs, stability
+    from paper_2105_01865_gb300.solver import Batch
+    boxes = inputs.batch_boxes(64, seed=4)
+    for box in boxes:
+        box["dt"] = 0.9 * stability.stable_dt(box["shape"], box["h"], box["bc"], box["cn"], box["pe"])
+    cells = sum(int(np.prod(b["shape"])) for b in boxes)
+    b = Batch(boxes, device=dev)
+    report = b.autotune(2)
+    st = b.stream
+    for _ in range(args.warmup):
+        b.step(1)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize(dev)
+    with torch.cuda.stream(st):
+        for a, c in ev:
+            flush.fill_(1)
+            a.record(st)
+            b.step(1)
+            c.record(st)
+    torch.cuda.synchronize(dev)
+    b.sync()
+    sec = sum(a.elapsed_time(c) for a, c in ev) / 1e3
+    sched = b.schedule()
+    out = dict(value=cells * args.steps / sec, unit="cell-updates/s", ms_per_step=1e3 * sec / args.steps,
+               boxes=len(boxes), cells=cells, dtype="f32",
+               schedule=dict(mode="persistent" if sched[0] == 0 else "phased", blocks_per_sm=sched[1],
+                             zchunk=sched[2], lpt=sched[3]),
+               launches_per_step=b.launches_per_step(), autotune_candidates=report.count("\n") - 1)
+    b.close()
+    return out
+
+
 def gpu_arm(args):
     import torch
     import torch.distributed as dist
@@ -256,17 +315,26 @@ def gpu_arm(args):
         ms = capi.ch_profile_step(s32.handle, 1)
         ksum = [a + b for a, b in zip(ksum, ms)]
     kms = [x / kreps for x in ksum]
-    # algorithmic bytes per cell of one launch (FP32): explicit averages the
-    # three substeps (24, 28, 28 B), x/y solves 8 B, z solve + update 12 B
-    kbytes = [80.0 / 3.0, 8.0, 8.0, 12.0]
     names = ["ch_explicit_rhs", "ch_solve_x", "ch_solve_y", "ch_solve_z_update"]
-    top = max(range(4), key=lambda k: kms[k])
-    peak, peak_src = measured_peak_hbm()
-    achieved = kbytes[top] * ncell / (kms[top] * 1e-3) / 1e9
-    roofline = dict(bound="hbm", kernel=names[top], achieved=achieved, peak=peak, unit="GB/s",
-                    frac=achieved / peak, traffic=None, peak_source=peak_src,
-                    kernels={n: dict(ms=m, algo_bytes_per_cell=b, gbs=b * ncell / (m * 1e-3) / 1e9)
-                             for n, m, b in zip(names, kms, kbytes)})
+    # algorithmic bytes per cell of one launch (FP32): the explicit kernel
+    # averages its three substeps (24, 28, 28 B), x/y solves 8 B, z solve +
+    # update 12 B; algorithmic FP32 flops per cell of the explicit kernel
+    # (3 WENO5 face reconstructions of ~75 flops, 7 psi', Laplacian, A_d
+    # fourth differences, divergence and the RK/CN combination)
+    kbytes = [80.0 / 3.0, 8.0, 8.0, 12.0]
+    explicit_flops = 300.0
+    peak_hbm, peak_src = measured_peak_hbm()
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    peak_fp32 = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12     # TFLOP/s: SMs x FP32 lanes x 2 flops x clock
+    traffic = recorded_traffic()
+    achieved = explicit_flops * ncell / (kms[0] * 1e-3) / 1e12
+    roofline = dict(bound="alu", kernel=names[0], achieved=achieved, peak=peak_fp32, unit="TFLOP/s",
+                    frac=achieved / peak_fp32, traffic=traffic.get(names[0]),
+                    peak_source=f"derived: 152 SMs x 128 FP32 lanes x 2 flops x {sm_mhz:.0f} MHz",
+                    kernels={n: dict(ms=m, algo_bytes_per_cell=b, gbs=b * ncell / (m * 1e-3) / 1e9,
+                                     hbm_frac=b * ncell / (m * 1e-3) / 1e9 / peak_hbm, traffic=traffic.get(n))
+                             for n, m, b in zip(names, kms, kbytes)},
+                    hbm_peak=dict(value=peak_hbm, unit="GB/s", source=peak_src))
 
     # end to end through the public API with host buffers: pinned H2D of C,
     # one step, D2H of C, every step
@@ -289,6 +357,8 @@ def gpu_arm(args):
     e2e = dict(value=ncell * args.steps * world / float(t), unit="cell-updates/s",
                h2d_bytes_per_step=ncell * 4, d2h_bytes_per_step=ncell * 4)
 
+    batched = batched_leg(args, dev, flush)
+
     # the plain FP64 GPU step on the same workload, for the precision speedup
     s64 = make("f64")
     k64 = max(3, args.steps // 4)
@@ -302,7 +372,7 @@ def gpu_arm(args):
                 config=dict(workload=W["name"], global_batch=world, seq_len=0,
                             parallelism=f"replicas{world}", cells=ncell, precision="f32 fields, f64 reductions",
                             l2="flushed between timed steps (256 MB write); working set 235 MB > L2"),
-                roofline=roofline, e2e=e2e, fp64_plain=fp64, clocks=clocks,
+                roofline=roofline, e2e=e2e, fp64_plain=fp64, batched=batched, clocks=clocks,
                 gpu_launches=args.steps * s32.launches_per_step())
     if rank == 0 and not args.no_cpu_baseline:
         cells, times = run_oracle(1, 0)
@@ -322,7 +392,7 @@ def gpu_arm(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
