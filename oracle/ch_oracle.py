@@ -136,9 +136,9 @@ def shifted(fp, g, d, s, shape):
 def lap_h(f, p: Params):
     """Second-order central 7-point Laplacian (Sec. 3, 'central second-order')."""
     fp = pad(f, p.bc, 1)
-    out = np.zeros(p.shape)
+    out = np.zeros(p.shape, dtype=np.result_type(f, 1.0))
     for d in range(3):
-        out += (shifted(fp, 1, d, 1, p.shape) - 2.0 * f + shifted(fp, 1, d, -1, p.shape)) / p.h ** 2
+        out = out + (shifted(fp, 1, d, 1, p.shape) - 2.0 * f + shifted(fp, 1, d, -1, p.shape)) / p.h ** 2
     return out
 
 
@@ -194,14 +194,14 @@ def face_fluxes(C, vel, p: Params, d):
 
 def advection(C, vel, p: Params):
     """-div(u C) = -sum_d (F_{f+1} - F_f) / h, conservative (Sec. 3)."""
-    out = np.zeros(p.shape)
+    out = np.zeros(p.shape, dtype=np.result_type(C, 1.0))
     for d in range(3):
         F = face_fluxes(C, vel[d], p, d)
         a = _axis(d)
         n = p.n(d)
         lower = np.take(F, np.arange(n), axis=a)
         upper = np.take(F, (np.arange(n) + 1) % F.shape[a], axis=a)
-        out -= (upper - lower) / p.h
+        out = out - (upper - lower) / p.h
     return out
 
 
@@ -280,9 +280,9 @@ def step(C, vel, p: Params, nsteps=1, psi_p=psi_prime):
     ``vel`` is None (u = 0) or a tuple (u, v, w) of face velocities with
     shapes (nz, ny, nfx), (nz, nfy, nx), (nfz, ny, nx).
     """
-    C = np.array(C, dtype=np.float64, copy=True)
+    C = np.array(C, dtype=np.result_type(C, np.float64), copy=True)
     for _ in range(nsteps):
-        Hprev = np.zeros(p.shape)
+        Hprev = np.zeros(p.shape, dtype=C.dtype)
         for l in range(3):
             C, Hprev = substep(C, Hprev, vel, p, l, psi_p)
     return C
