@@ -163,6 +163,30 @@ int ch_launches_per_step(const ch_handle* h);
 int ch_profile_step(ch_handle* h, int64_t nsteps, double* ms_out);
 
 /* ---------------------------------------------------------------------------
+ * Differentiation form (u = 0): the adjoint of nsteps steps.  The paper has
+ * no derivative; this is the exact transpose of the discrete step of Sec. 3
+ * (line solves, A_d, lap psi', the RK3 history term and the M-dependence of
+ * the factorised operator), evaluated in the handle's precision with FP64
+ * dot products for dL/dM.
+ * ------------------------------------------------------------------------- */
+
+/* Device workspace bytes for ch_step_adjoint (checkpoints every ckpt_every
+ * steps, one recomputed segment, 15 scratch fields); 0 if unsupported
+ * (advect = 1) or invalid. */
+size_t ch_adjoint_workspace_bytes(const ch_handle* h, int64_t nsteps, int64_t ckpt_every);
+
+/* Reverse nsteps steps of the handle's problem started from C0 (device field,
+ * not modified): given lam_T = dL/dC_T (device field), write lam_0 = dL/dC_0
+ * (device field) and *dL_dM = dL/dM through every occurrence of M = 1/Pe
+ * (host double).  The forward trajectory is recomputed from checkpoints
+ * stored every ckpt_every steps (memory ~ (nsteps/ckpt_every + ckpt_every)
+ * fields, work ~ 2 forward passes + the reverse).  Does not touch the handle's
+ * C.  Waits for the stream.  Errors: CH_EINVAL (advect = 1, bad args),
+ * CH_ENOMEM (workspace too small), CH_ECUDA. */
+int ch_step_adjoint(ch_handle* h, const void* C0, int64_t nsteps, int64_t ckpt_every, const void* lam_T, void* lam_0,
+                    double* dL_dM, void* work, size_t work_bytes);
+
+/* ---------------------------------------------------------------------------
  * Batched form: many independent boxes of uneven sizes and parameters
  * (each box is the Sec. 3 step of its own ch_params) advanced together.  The
  * paper advances one box; batching is this library's addition.

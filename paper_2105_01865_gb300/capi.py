@@ -64,6 +64,9 @@ SIGNATURES = [
     ("ch_profile_step", ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]),
     ("ch_mass_noalloc", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
                                         ctypes.c_int, _P, _P]),
+    ("ch_adjoint_workspace_bytes", ctypes.c_size_t, [_P, ctypes.c_int64, ctypes.c_int64]),
+    ("ch_step_adjoint", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, _P, _P, ctypes.POINTER(ctypes.c_double),
+                                       _P, ctypes.c_size_t]),
     ("ch_batch_workspace_bytes", ctypes.c_size_t, [ctypes.POINTER(ch_params), ctypes.c_int]),
     ("ch_batch_create", ctypes.c_int, [ctypes.POINTER(ch_params), ctypes.c_int, ctypes.POINTER(_P), _P, ctypes.c_size_t,
                                        _P, ctypes.POINTER(_P)]),
@@ -212,6 +215,18 @@ def ch_mass_noalloc(C, h, out, stream):
     st = load().ch_mass_noalloc(_ptr(C), nx, ny, nz, h, prec, _ptr(out), ctypes.c_void_p(stream.cuda_stream))
     if st != CH_OK:
         raise CHError(st, f"ch_mass_noalloc: {ch_error_string(st)} (grid limit 268435456 cells)")
+
+
+def ch_adjoint_workspace_bytes(handle, nsteps, ckpt_every):
+    return int(load().ch_adjoint_workspace_bytes(handle, nsteps, ckpt_every))
+
+
+def ch_step_adjoint(handle, C0, nsteps, ckpt_every, lam_T, lam_0, work):
+    """C0, lam_T, lam_0, work: torch CUDA tensors.  Returns dL/dM."""
+    out = ctypes.c_double()
+    _check(load().ch_step_adjoint(handle, _ptr(C0), nsteps, ckpt_every, _ptr(lam_T), _ptr(lam_0), ctypes.byref(out),
+                                  _ptr(work), work.numel() * work.element_size()), handle, "ch_step_adjoint")
+    return out.value
 
 
 def _bcheck(status, batch, what):

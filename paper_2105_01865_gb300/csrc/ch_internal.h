@@ -85,6 +85,11 @@ inline int fail(ch_handle* h, int code, const char* fmt, ...) {
                              cudaGetErrorString(e_), __FILE__, __LINE__);                  \
     } while (0)
 
+// launchers shared with the adjoint (ch_step.cu), in the handle's precision
+int launch_explicit_any(ch_handle* h, int l, const void* C, const void* Hprev, void* Hout, void* r);
+int launch_solve_any(ch_handle* h, int l, int dir, void* a, void* Cupd);
+int launch_step_any(ch_handle* h, void* C);  // one full step of the field C (direct launches)
+
 // multi-resolution entry points implemented in ch_mr.cu
 int mr_build_tables(ch_handle* h, const double* xf, const double* yf, const double* zf);
 void mr_destroy(ch_handle* h);

@@ -124,10 +124,11 @@ WCoef<T> wcoef(const LineTables& lt) {
     return k;
 }
 
+// Solve (I + c A_dir) x = a in place along direction dir for substep l's c;
+// for dir = 2 with Cupd != nullptr the solution is added to Cupd instead.
 template <typename T, int M>
-int launch_solves_m(ch_handle* h, int l, int dir, cudaEvent_t ev_after) {
+int launch_solves_m(ch_handle* h, int l, int dir, T* r, T* Cupd, cudaEvent_t ev_after) {
     const int nx = (int)h->n[0], ny = (int)h->n[1], nz = (int)h->n[2];
-    T* r = (T*)h->r;
     const WCoef<T> cf = wcoef<T>(h->lines[dir][l]);
     if (dir == 0) {
         const int64_t nlines = (int64_t)ny * nz;
@@ -139,9 +140,12 @@ int launch_solves_m(ch_handle* h, int l, int dir, cudaEvent_t ev_after) {
         if (dir == 1)
             ch_solve_yz<T, M, false><<<xblocks * (unsigned)nz, YZShape<T, M>::kWarps * 32, shm, h->stream>>>(
                 r, nullptr, nx, (int64_t)nx * ny, nx, cf, h->status);
-        else
+        else if (Cupd)
             ch_solve_yz<T, M, true><<<xblocks * (unsigned)ny, YZShape<T, M>::kWarps * 32, shm, h->stream>>>(
-                r, (T*)h->C, nx, nx, (int64_t)nx * ny, cf, h->status);
+                r, Cupd, nx, nx, (int64_t)nx * ny, cf, h->status);
+        else
+            ch_solve_yz<T, M, false><<<xblocks * (unsigned)ny, YZShape<T, M>::kWarps * 32, shm, h->stream>>>(
+                r, nullptr, nx, nx, (int64_t)nx * ny, cf, h->status);
     }
     CHG_CUDA(h, cudaGetLastError());
     if (ev_after) CHG_CUDA(h, cudaEventRecord(ev_after, h->stream));
@@ -149,14 +153,14 @@ int launch_solves_m(ch_handle* h, int l, int dir, cudaEvent_t ev_after) {
 }
 
 template <typename T>
-int launch_solve(ch_handle* h, int l, int dir, cudaEvent_t ev_after) {
+int launch_solve(ch_handle* h, int l, int dir, T* r, T* Cupd, cudaEvent_t ev_after) {
     switch (h->lines[dir][l].M) {
-        case 1: return launch_solves_m<T, 1>(h, l, dir, ev_after);
-        case 2: return launch_solves_m<T, 2>(h, l, dir, ev_after);
-        case 4: return launch_solves_m<T, 4>(h, l, dir, ev_after);
-        case 8: return launch_solves_m<T, 8>(h, l, dir, ev_after);
-        case 16: return launch_solves_m<T, 16>(h, l, dir, ev_after);
-        case 32: return launch_solves_m<T, 32>(h, l, dir, ev_after);
+        case 1: return launch_solves_m<T, 1>(h, l, dir, r, Cupd, ev_after);
+        case 2: return launch_solves_m<T, 2>(h, l, dir, r, Cupd, ev_after);
+        case 4: return launch_solves_m<T, 4>(h, l, dir, r, Cupd, ev_after);
+        case 8: return launch_solves_m<T, 8>(h, l, dir, r, Cupd, ev_after);
+        case 16: return launch_solves_m<T, 16>(h, l, dir, r, Cupd, ev_after);
+        case 32: return launch_solves_m<T, 32>(h, l, dir, r, Cupd, ev_after);
         default: return fail(h, CH_EINVAL, "unsupported line length");
     }
 }
@@ -170,8 +174,9 @@ int set_attrs_m(ch_handle* h) {
     return CH_OK;
 }
 
+// Explicit RHS of substep l from C (and Hprev) into Hout and r.
 template <typename T>
-int launch_substep(ch_handle* h, int l, cudaEvent_t* ev = nullptr) {
+int launch_explicit(ch_handle* h, int l, const T* C, const T* Hprev, T* Hout, T* r, cudaEvent_t* ev) {
     const ch_params& p = h->p;
     const int nx = (int)h->n[0], ny = (int)h->n[1], nz = (int)h->n[2];
     RhsArgs<T> a;
@@ -195,10 +200,6 @@ int launch_substep(ch_handle* h, int l, cudaEvent_t* ev = nullptr) {
     a.impl = (T)(alpha * p.dt * mob * kappa);
     a.eps = (T)p.weno_eps;
     a.has_prev = kRho[l] != 0.0;
-    T* C = (T*)h->C;
-    T* Hout = (T*)h->H[l & 1];
-    const T* Hprev = (const T*)h->H[(l + 1) & 1];
-    T* r = (T*)h->r;
     const T* u = p.advect ? (const T*)h->vel[0] : nullptr;
     const T* v = p.advect ? (const T*)h->vel[1] : nullptr;
     const T* w = p.advect ? (const T*)h->vel[2] : nullptr;
@@ -220,10 +221,18 @@ int launch_substep(ch_handle* h, int l, cudaEvent_t* ev = nullptr) {
     }
     CHG_CUDA(h, cudaGetLastError());
     if (ev) CHG_CUDA(h, cudaEventRecord(ev[1], h->stream));
+    return CH_OK;
+}
 
+template <typename T>
+int launch_substep(ch_handle* h, int l, cudaEvent_t* ev = nullptr) {
+    T* C = (T*)h->C;
+    T* r = (T*)h->r;
+    int rc = launch_explicit<T>(h, l, C, (const T*)h->H[(l + 1) & 1], (T*)h->H[l & 1], r, ev);
+    if (rc != CH_OK) return rc;
     // x solve (Eq. eq-fac-1), y solve (Eq. eq-fac-2), z solve + update (Eq. eq-fac-3)
     for (int dir = 0; dir < 3; ++dir) {
-        const int rc = launch_solve<T>(h, l, dir, ev ? ev[2 + dir] : nullptr);
+        rc = launch_solve<T>(h, l, dir, r, dir == 2 ? C : nullptr, ev ? ev[2 + dir] : nullptr);
         if (rc != CH_OK) return rc;
     }
     return CH_OK;
@@ -240,6 +249,35 @@ int set_smem_attrs(ch_handle* h) {
     if (rc == CH_OK) rc = set_attrs_m<T, 32>(h);
     return rc;
 }
+
+}  // namespace
+
+namespace chg {
+
+int launch_explicit_any(ch_handle* h, int l, const void* C, const void* Hprev, void* Hout, void* r) {
+    if (h->prec == CH_F64)
+        return launch_explicit<double>(h, l, (const double*)C, (const double*)Hprev, (double*)Hout, (double*)r, nullptr);
+    return launch_explicit<float>(h, l, (const float*)C, (const float*)Hprev, (float*)Hout, (float*)r, nullptr);
+}
+
+int launch_solve_any(ch_handle* h, int l, int dir, void* a, void* Cupd) {
+    if (h->prec == CH_F64) return launch_solve<double>(h, l, dir, (double*)a, (double*)Cupd, nullptr);
+    return launch_solve<float>(h, l, dir, (float*)a, (float*)Cupd, nullptr);
+}
+
+int launch_step_any(ch_handle* h, void* C) {
+    void* saved = h->C;
+    h->C = C;
+    int rc = CH_OK;
+    for (int l = 0; l < kRK && rc == CH_OK; ++l)
+        rc = h->prec == CH_F64 ? launch_substep<double>(h, l) : launch_substep<float>(h, l);
+    h->C = saved;
+    return rc;
+}
+
+}  // namespace chg
+
+namespace {
 
 int launch_step(ch_handle* h) {
     for (int l = 0; l < kRK; ++l) {

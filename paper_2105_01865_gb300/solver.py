@@ -99,6 +99,19 @@ class Solver:
     def launches_per_step(self):
         return capi.ch_launches_per_step(self.handle)
 
+    def adjoint(self, C0, nsteps, lam_T, ckpt_every=10):
+        """dL/dC0 and dL/dM of nsteps steps from C0, given lam_T = dL/dC_T.
+        C0 and lam_T are numpy arrays or CUDA tensors; returns (tensor, float)."""
+        C0d, lamd = self._dev(C0), self._dev(lam_T)
+        lam0 = torch.empty_like(C0d)
+        nbytes = capi.ch_adjoint_workspace_bytes(self.handle, nsteps, ckpt_every)
+        if nbytes == 0:
+            raise capi.CHError(capi.CH_EINVAL, "adjoint unsupported for these parameters (u must be 0)")
+        work = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self._order()
+        dM = capi.ch_step_adjoint(self.handle, C0d, nsteps, ckpt_every, lamd, lam0, work)
+        return lam0, dM
+
     def close(self):
         if getattr(self, "handle", None) is not None:
             self.stream.synchronize()
