@@ -205,15 +205,20 @@ def recorded_traffic():
     return rec.get("bytes_per_launch", {})
 
 
-def batched_leg(args, dev, flush):
-    """The batched form on 64 uneven periodic boxes (32^3 .. 128^3), u = 0."""
+def batched_leg(args, dev, flush, rank=0, world=1):
+    """The batched form on 64 uneven periodic boxes (32^3 .. 128^3), u = 0.
+    With several ranks the boxes are placed by LPT on cell counts (no
+    collective on the data path); the time is the max over ranks."""
     import torch
     from paper_2105_01865_gb300 import inputs, stability
+    from paper_2105_01865_gb300.sharding import lpt_assign, max_over_ranks
     from paper_2105_01865_gb300.solver import Batch
-    boxes = inputs.batch_boxes(64, seed=4)
+    all_boxes = inputs.batch_boxes(64, seed=4)
+    cells_all = [int(np.prod(b["shape"])) for b in all_boxes]
+    boxes = [all_boxes[i] for i in lpt_assign(cells_all, world)[rank]]
     for box in boxes:
         box["dt"] = 0.9 * stability.stable_dt(box["shape"], box["h"], box["bc"], box["cn"], box["pe"])
-    cells = sum(int(np.prod(b["shape"])) for b in boxes)
+    cells = sum(cells_all)
     b = Batch(boxes, device=dev)
     report = b.autotune(2)
     st = b.stream
@@ -229,14 +234,65 @@ def batched_leg(args, dev, flush):
             c.record(st)
     torch.cuda.synchronize(dev)
     b.sync()
-    sec = sum(a.elapsed_time(c) for a, c in ev) / 1e3
+    sec = max_over_ranks(sum(a.elapsed_time(c) for a, c in ev) / 1e3)
     sched = b.schedule()
     out = dict(value=cells * args.steps / sec, unit="cell-updates/s", ms_per_step=1e3 * sec / args.steps,
-               boxes=len(boxes), cells=cells, dtype="f32",
+               boxes=len(all_boxes), cells=cells, dtype="f32", placement="LPT on cell counts, no collective",
                schedule=dict(mode="persistent" if sched[0] == 0 else "phased", blocks_per_sm=sched[1],
                              zchunk=sched[2], lpt=sched[3]),
                launches_per_step=b.launches_per_step(), autotune_candidates=report.count("\n") - 1)
     b.close()
+    return out
+
+
+def multires_leg(args, dev, flush):
+    """Multiple-resolution workload: seeded divergence-free coarse velocity on
+    a 256 x 256 x 128 mesh (tanh-stretched z, walls at z = 0, 1) transferred
+    to the 1024 x 1024 x 512 uniform FP32 fine mesh holding ~1000 drops of
+    radius U[0.01, 0.03]; times the transfer and the fine CH step."""
+    import torch
+    from paper_2105_01865_gb300 import inputs, stability
+    from paper_2105_01865_gb300.solver import Solver
+    nx, ny, nz = 1024, 1024, 512
+    h = 1.0 / nz
+    bc = (0, 0, 1)
+    cn = 0.75 * h
+    pe = 0.9 / cn
+    xf, yf = inputs.uniform_faces(256, 2.0), inputs.uniform_faces(256, 2.0)
+    zf = inputs.stretched_faces(128, 1.0, 2.0)
+    uc, vc, wc = inputs.curl_velocity(xf, yf, zf, bc, 3, kmax=8)
+    rng = np.random.Generator(np.random.PCG64(3))
+    centres, radii = inputs.random_drops(rng, 1000, (2.0, 2.0, 1.0), 0.01, 0.03, 4 * cn, (True, True, True))
+    C0 = inputs.drops_field_local((nz, ny, nx), h, centres, radii, cn, 8 * cn)
+    dt = min(0.9 * stability.stable_dt((nz, ny, nx), h, bc, cn, pe), 0.5 * h / 1.0)
+    s = Solver((nz, ny, nx), h, bc, cn, pe, dt, C0, precision="f32", coarse_faces=(xf, yf, zf), device=dev)
+    s.set_velocity_coarse(uc, vc, wc)
+    st = s.stream
+
+    def timed(fn, reps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        torch.cuda.synchronize(dev)
+        with torch.cuda.stream(st):
+            for a, c in ev:
+                flush.fill_(1)
+                a.record(st)
+                fn()
+                c.record(st)
+        torch.cuda.synchronize(dev)
+        return sum(a.elapsed_time(c) for a, c in ev) / reps
+
+    s.interp_to_fine()
+    interp_ms = timed(s.interp_to_fine, 3)
+    for _ in range(3):
+        s.step(1)
+    k = max(3, min(args.steps, 20))
+    step_ms = timed(lambda: s.step(1), k)
+    s.sync()
+    cells = nx * ny * nz
+    out = dict(value=cells / (step_ms * 1e-3), unit="cell-updates/s", step_ms=step_ms, interp_ms=interp_ms,
+               cells=cells, coarse_cells=256 * 256 * 128, drops=len(radii), steps=k, dtype="f32",
+               interp_fine_faces_gbs=3 * cells * 4 / (interp_ms * 1e-3) / 1e9)
+    s.close()
     return out
 
 
@@ -294,11 +350,12 @@ def gpu_arm(args):
         barrier()
         return sum(a.elapsed_time(b) for a, b in ev) / 1e3
 
-    # main FP32 line
+    # main FP32 line; nvidia-smi samples the clocks from here through the
+    # batched and multi-resolution legs (all timed regions of this run)
     s32 = make("f32")
-    with ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local) as clk:
-        sec = timed(s32, args.steps, args.warmup)
-    clocks = clk.summary()
+    clk = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    clk.__enter__()
+    sec = timed(s32, args.steps, args.warmup)
     s32.sync()
     sec_t = torch.tensor([sec], device=dev, dtype=torch.float64)
     if world > 1:
@@ -324,7 +381,7 @@ def gpu_arm(args):
     kbytes = [80.0 / 3.0, 8.0, 8.0, 12.0]
     explicit_flops = 300.0
     peak_hbm, peak_src = measured_peak_hbm()
-    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    sm_mhz = 2070.0  # the maximum SM clock; the sampled median is reported in "clocks"
     peak_fp32 = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12     # TFLOP/s: SMs x FP32 lanes x 2 flops x clock
     traffic = recorded_traffic()
     achieved = explicit_flops * ncell / (kms[0] * 1e-3) / 1e12
@@ -357,7 +414,10 @@ def gpu_arm(args):
     e2e = dict(value=ncell * args.steps * world / float(t), unit="cell-updates/s",
                h2d_bytes_per_step=ncell * 4, d2h_bytes_per_step=ncell * 4)
 
-    batched = batched_leg(args, dev, flush)
+    batched = batched_leg(args, dev, flush, rank, world)
+    multires = multires_leg(args, dev, flush) if not args.no_multires else None
+    clk.__exit__(None, None, None)
+    clocks = clk.summary()
 
     # the plain FP64 GPU step on the same workload, for the precision speedup
     s64 = make("f64")
@@ -372,7 +432,7 @@ def gpu_arm(args):
                 config=dict(workload=W["name"], global_batch=world, seq_len=0,
                             parallelism=f"replicas{world}", cells=ncell, precision="f32 fields, f64 reductions",
                             l2="flushed between timed steps (256 MB write); working set 235 MB > L2"),
-                roofline=roofline, e2e=e2e, fp64_plain=fp64, batched=batched, clocks=clocks,
+                roofline=roofline, e2e=e2e, fp64_plain=fp64, batched=batched, multires=multires, clocks=clocks,
                 gpu_launches=args.steps * s32.launches_per_step())
     if rank == 0 and not args.no_cpu_baseline:
         cells, times = run_oracle(1, 0)
@@ -396,6 +456,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-multires", action="store_true", help="skip the 1024x1024x512 transfer + step leg")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
