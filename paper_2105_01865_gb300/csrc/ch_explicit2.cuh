@@ -102,8 +102,15 @@ __device__ __forceinline__ Pr<T> face_flux_p(Pr<T> vel, Pr<T> m3, Pr<T> m2, Pr<T
     return mul(vel, weno5p(a1, a2, a3, a4, a5, eps));
 }
 
-constexpr int kTX2 = 64;  // cells in x per CTA (two per thread)
-constexpr int kTZ2 = 8;   // z-planes marched per CTA
+// Tuning knobs (compile-time; the defaults are the measured best on GB300)
+#ifndef CH_EXPLICIT_MIN_BLOCKS
+#define CH_EXPLICIT_MIN_BLOCKS 3
+#endif
+#ifndef CH_EXPLICIT_TZ
+#define CH_EXPLICIT_TZ 8
+#endif
+constexpr int kTX2 = 64;               // cells in x per CTA (two per thread)
+constexpr int kTZ2 = CH_EXPLICIT_TZ;   // z-planes marched per CTA
 constexpr int kHL2 = 4;   // left halo columns (even, so thread pairs stay 8/16-byte aligned)
 
 // One 64 x 8 x zchunk tile (tile coordinates bx, by, bz) computed by the 256
@@ -293,7 +300,7 @@ __device__ __forceinline__ void explicit_tile2(const T* C, const T* u, const T* 
 }
 
 template <typename T, bool ADV>
-__global__ void __launch_bounds__(32 * kTY, sizeof(T) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(32 * kTY, sizeof(T) == 4 ? CH_EXPLICIT_MIN_BLOCKS : 2)
 ch_explicit_rhs2(const T* __restrict__ C, const T* __restrict__ u, const T* __restrict__ v,
                  const T* __restrict__ w, const T* __restrict__ Hprev, T* __restrict__ Hout, T* __restrict__ r,
                  RhsArgs<T> a) {

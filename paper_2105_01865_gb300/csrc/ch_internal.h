@@ -26,6 +26,8 @@ struct LineTables {
     int n;             // cells along the line
     int M;             // rows per lane (32 M >= n)
     int periodic;
+    const void* col;   // column-solver block (col_layout(nw, R)), or null
+    int nw, R;         // column-solver warps per CTA and rows per warp
 };
 
 }  // namespace chg

@@ -589,6 +589,186 @@ ch_solve_yz(T* __restrict__ a, T* __restrict__ Cf, int nx, int64_t outer_stride,
 }
 
 // ---------------------------------------------------------------------------
+// Column solver for y- and z-lines: the 32 lanes of a warp own 32 adjacent
+// lines (consecutive x, so every row access is one coalesced 128-byte line),
+// and warp w of the CTA owns rows [w R, w R + R) of all 32 lines in
+// registers.  Each warp runs its row chunk from a zero state; the chunk end
+// states are composed across warps through shared memory with the chunks'
+// 2x2 transfer matrices (host-precomputed), then each warp reruns its chunk.
+// Rows stream straight between HBM and registers: no staging tile.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct CCoef {
+    const T* __restrict__ fwd;  // [rows][4]: l1, l2, 1/u0, 0
+    const T* __restrict__ bwd;  // [rows][2]: u1/u0, u2/u0
+    const T* __restrict__ W;    // [rows][4]  periodic only
+    const T* __restrict__ Z;    // [rows][4]  periodic only
+    const T* __restrict__ P;    // [NW][4]    forward chunk transfer matrices
+    const T* __restrict__ Q;    // [NW][4]    backward chunk transfer matrices
+    const T* __restrict__ S;    // [4][4]
+    int n;
+    int periodic;
+};
+
+// Coefficient loads of the column solver.  They are volatile so that the
+// compiler reloads a row's coefficients in each pass (they are L1-resident)
+// instead of keeping R rows of them live in registers between passes.
+__device__ __forceinline__ V4<float> ldv4(const float* p) {
+    V4<float> r;
+    asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+                 : "l"(p));
+    return r;
+}
+__device__ __forceinline__ V4<double> ldv4(const double* p) {
+    V4<double> r;
+    asm volatile("ld.global.nc.v2.f64 {%0, %1}, [%2];" : "=d"(r.x), "=d"(r.y) : "l"(p));
+    asm volatile("ld.global.nc.v2.f64 {%0, %1}, [%2];" : "=d"(r.z), "=d"(r.w) : "l"(p + 2));
+    return r;
+}
+__device__ __forceinline__ void ldv2(const float* p, float& a, float& b) {
+    asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(a), "=f"(b) : "l"(p));
+}
+__device__ __forceinline__ void ldv2(const double* p, double& a, double& b) {
+    asm volatile("ld.global.nc.v2.f64 {%0, %1}, [%2];" : "=d"(a), "=d"(b) : "l"(p));
+}
+
+template <typename T, int R, int NW, bool UPDATE>
+__global__ void __launch_bounds__(NW * 32, 1024 / (NW * 32))
+ch_solve_cols(T* __restrict__ a, T* __restrict__ Cf, int nx, int64_t outer_stride, int64_t line_stride, CCoef<T> cf,
+              unsigned int* status) {
+    __shared__ T fq[NW][2][32];
+    __shared__ T bq[NW][2][32];
+    __shared__ T wacc[NW][4][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int xblocks = (nx + 31) >> 5;
+    const int xb = blockIdx.x % xblocks;
+    const int64_t outer = blockIdx.x / xblocks;
+    const int i0 = xb * 32;
+    const bool valid = i0 + lane < nx;
+    const int64_t base = outer * outer_stride + i0 + lane;
+    const int n = cf.n;
+    const int j0 = w * R;
+    const bool per = cf.periodic;
+    T v[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int j = j0 + i;
+        v[i] = (valid && j < n) ? a[base + (int64_t)j * line_stride] : T(0);
+    }
+    // forward elimination from a zero state over this warp's rows
+    T y1 = T(0), y2 = T(0), acc0 = T(0), acc1 = T(0), acc2 = T(0), acc3 = T(0);
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const V4<T> c = ldv4(cf.fwd + 4 * (j0 + i));
+        const T y = (v[i] - c.y * y2) - c.x * y1;
+        y2 = y1;
+        y1 = y;
+        if (per) {
+            const V4<T> ww = ldv4(cf.W + 4 * (j0 + i));
+            acc0 += ww.x * v[i];
+            acc1 += ww.y * v[i];
+            acc2 += ww.z * v[i];
+            acc3 += ww.w * v[i];
+        }
+    }
+    fq[w][0][lane] = y1;
+    fq[w][1][lane] = y2;
+    if (per) {
+        wacc[w][0][lane] = acc0;
+        wacc[w][1][lane] = acc1;
+        wacc[w][2][lane] = acc2;
+        wacc[w][3][lane] = acc3;
+    }
+    __syncthreads();
+    // incoming state: compose the chunks of warps 0 .. w-1
+    T s0 = T(0), s1 = T(0);
+    for (int u = 0; u < w; ++u) {
+        const V4<T> Pm = ld4(cf.P + 4 * u);
+        const T n0 = Pm.x * s0 + Pm.y * s1 + fq[u][0][lane];
+        const T n1 = Pm.z * s0 + Pm.w * s1 + fq[u][1][lane];
+        s0 = n0;
+        s1 = n1;
+    }
+    T sv0 = T(0), sv1 = T(0), sv2 = T(0), sv3 = T(0);
+    if (per) {
+        T t0 = T(0), t1 = T(0), t2 = T(0), t3 = T(0);
+#pragma unroll
+        for (int u = 0; u < NW; ++u) {
+            t0 += wacc[u][0][lane];
+            t1 += wacc[u][1][lane];
+            t2 += wacc[u][2][lane];
+            t3 += wacc[u][3][lane];
+        }
+        const V4<T> r0 = ld4(cf.S), r1 = ld4(cf.S + 4), r2 = ld4(cf.S + 8), r3 = ld4(cf.S + 12);
+        sv0 = r0.x * t0 + r0.y * t1 + r0.z * t2 + r0.w * t3;
+        sv1 = r1.x * t0 + r1.y * t1 + r1.z * t2 + r1.w * t3;
+        sv2 = r2.x * t0 + r2.y * t1 + r2.z * t2 + r2.w * t3;
+        sv3 = r3.x * t0 + r3.y * t1 + r3.z * t2 + r3.w * t3;
+    }
+    y1 = s0;
+    y2 = s1;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const V4<T> c = ldv4(cf.fwd + 4 * (j0 + i));
+        const T y = (v[i] - c.y * y2) - c.x * y1;
+        y2 = y1;
+        y1 = y;
+        v[i] = y * c.z;
+    }
+    // back substitution from a zero state over this warp's rows
+    T x1 = T(0), x2 = T(0);
+#pragma unroll
+    for (int i = R - 1; i >= 0; --i) {
+        T u1, u2;
+        ldv2(cf.bwd + 2 * (j0 + i), u1, u2);
+        const T x = (v[i] - u2 * x2) - u1 * x1;
+        x2 = x1;
+        x1 = x;
+    }
+    bq[w][0][lane] = x1;
+    bq[w][1][lane] = x2;
+    __syncthreads();
+    s0 = T(0);
+    s1 = T(0);
+    for (int u = NW - 1; u > w; --u) {
+        const V4<T> Qm = ld4(cf.Q + 4 * u);
+        const T n0 = Qm.x * s0 + Qm.y * s1 + bq[u][0][lane];
+        const T n1 = Qm.z * s0 + Qm.w * s1 + bq[u][1][lane];
+        s0 = n0;
+        s1 = n1;
+    }
+    x1 = s0;
+    x2 = s1;
+    bool bad = false;
+#pragma unroll
+    for (int i = R - 1; i >= 0; --i) {
+        T u1, u2;
+        ldv2(cf.bwd + 2 * (j0 + i), u1, u2);
+        const T x = (v[i] - u2 * x2) - u1 * x1;
+        x2 = x1;
+        x1 = x;
+        T o = x;
+        if (per) {
+            const V4<T> z = ldv4(cf.Z + 4 * (j0 + i));
+            o -= z.x * sv0 + z.y * sv1 + z.z * sv2 + z.w * sv3;
+        }
+        const int j = j0 + i;
+        if (valid && j < n) {
+            const int64_t idx = base + (int64_t)j * line_stride;
+            if (UPDATE) {
+                const T cnew = Cf[idx] + o;
+                bad |= !isfinite(cnew);
+                Cf[idx] = cnew;
+            } else {
+                a[idx] = o;
+            }
+        }
+    }
+    if (UPDATE && bad) atomicOr(status, 1u);
+}
+
+// ---------------------------------------------------------------------------
 // FP64 reductions: block partial sums (warp shuffles + shared memory), then a
 // single-block pass in fixed order, so results are deterministic.
 // ---------------------------------------------------------------------------

@@ -153,7 +153,75 @@ int launch_solves_m(ch_handle* h, int l, int dir, T* r, T* Cupd, cudaEvent_t ev_
 }
 
 template <typename T>
+CCoef<T> ccoef(const LineTables& lt) {
+    const ColLayout L = col_layout(lt.nw, lt.R);
+    const T* b = (const T*)lt.col;
+    CCoef<T> k;
+    k.fwd = b + L.fwd;
+    k.bwd = b + L.bwd;
+    k.W = b + L.W;
+    k.Z = b + L.Z;
+    k.P = b + L.P;
+    k.Q = b + L.Q;
+    k.S = b + L.S;
+    k.n = lt.n;
+    k.periodic = lt.periodic;
+    return k;
+}
+
+template <typename T, int R, int NW>
+int launch_cols_rn(ch_handle* h, int l, int dir, T* r, T* Cupd) {
+    const int nx = (int)h->n[0], ny = (int)h->n[1], nz = (int)h->n[2];
+    const CCoef<T> cf = ccoef<T>(h->lines[dir][l]);
+    const unsigned xblocks = (unsigned)((nx + 31) / 32);
+    if (dir == 1)
+        ch_solve_cols<T, R, NW, false><<<xblocks * (unsigned)nz, NW * 32, 0, h->stream>>>(
+            r, nullptr, nx, (int64_t)nx * ny, nx, cf, h->status);
+    else if (Cupd)
+        ch_solve_cols<T, R, NW, true><<<xblocks * (unsigned)ny, NW * 32, 0, h->stream>>>(
+            r, Cupd, nx, nx, (int64_t)nx * ny, cf, h->status);
+    else
+        ch_solve_cols<T, R, NW, false><<<xblocks * (unsigned)ny, NW * 32, 0, h->stream>>>(
+            r, nullptr, nx, nx, (int64_t)nx * ny, cf, h->status);
+    CHG_CUDA(h, cudaGetLastError());
+    return CH_OK;
+}
+
+// Which strided directions use the column solver (bit 1: y, bit 2: z); the
+// others use the shared-memory tile solver.  Default: z only (measured).
+#ifndef CH_COLUMN_DIRS
+#define CH_COLUMN_DIRS 4
+#endif
+
+// Column solver for y/z lines (shape chosen by col_shape); -1 if none.
+template <typename T>
+int launch_cols(ch_handle* h, int l, int dir, T* r, T* Cupd) {
+    const LineTables& lt = h->lines[dir][l];
+    if (!lt.col || !((CH_COLUMN_DIRS >> dir) & 1)) return -1;
+    if (lt.nw == 8) {
+        switch (lt.R) {
+            case 1: return launch_cols_rn<T, 1, 8>(h, l, dir, r, Cupd);
+            case 2: return launch_cols_rn<T, 2, 8>(h, l, dir, r, Cupd);
+            case 4: return launch_cols_rn<T, 4, 8>(h, l, dir, r, Cupd);
+            case 8: return launch_cols_rn<T, 8, 8>(h, l, dir, r, Cupd);
+            case 16: return launch_cols_rn<T, 16, 8>(h, l, dir, r, Cupd);
+            default: return -1;
+        }
+    }
+    if (lt.nw == 16 && lt.R == 16) return launch_cols_rn<T, 16, 16>(h, l, dir, r, Cupd);
+    if (lt.nw == 32 && lt.R == 16) return launch_cols_rn<T, 16, 32>(h, l, dir, r, Cupd);
+    return -1;
+}
+
+template <typename T>
 int launch_solve(ch_handle* h, int l, int dir, T* r, T* Cupd, cudaEvent_t ev_after) {
+    if (dir > 0) {
+        const int rc = launch_cols<T>(h, l, dir, r, Cupd);
+        if (rc >= 0) {
+            if (rc == CH_OK && ev_after) CHG_CUDA(h, cudaEventRecord(ev_after, h->stream));
+            return rc;
+        }
+    }
     switch (h->lines[dir][l].M) {
         case 1: return launch_solves_m<T, 1>(h, l, dir, r, Cupd, ev_after);
         case 2: return launch_solves_m<T, 2>(h, l, dir, r, Cupd, ev_after);
@@ -377,6 +445,17 @@ int ch_create(const ch_params* p, void* C, void* work, size_t work_bytes, void* 
                 lt.M = mch;
                 lt.periodic = F.periodic;
                 total += align_up(all.back().size() * h->esz);
+                // y and z lines also get column-solver tables when they fit
+                int nw = 0, R = 0;
+                if (d > 0 && col_shape(n, &nw, &R)) {
+                    lt.nw = nw;
+                    lt.R = R;
+                    all.push_back(col_tables(F, nw, R));
+                } else {
+                    lt.nw = lt.R = 0;
+                    all.push_back({});
+                }
+                total += align_up(all.back().size() * h->esz);
             }
         if (cudaMalloc(&h->coef_buf, total) != cudaSuccess) {
             free(h);
@@ -384,7 +463,7 @@ int ch_create(const ch_params* p, void* C, void* work, size_t work_bytes, void* 
         }
         std::vector<unsigned char> host(total, 0);
         size_t off = 0;
-        for (int q = 0; q < 3 * kRK; ++q) {
+        for (int q = 0; q < 2 * 3 * kRK; ++q) {
             const std::vector<double>& v = all[q];
             unsigned char* dst = host.data() + off;
             for (size_t e = 0; e < v.size(); ++e) {
@@ -393,7 +472,11 @@ int ch_create(const ch_params* p, void* C, void* work, size_t work_bytes, void* 
                 else
                     ((float*)dst)[e] = (float)v[e];
             }
-            h->lines[q / kRK][q % kRK].base = (char*)h->coef_buf + off;
+            LineTables& lt = h->lines[(q / 2) / kRK][(q / 2) % kRK];
+            if (q % 2 == 0)
+                lt.base = (char*)h->coef_buf + off;
+            else
+                lt.col = v.empty() ? nullptr : (char*)h->coef_buf + off;
             off += align_up(v.size() * h->esz);
         }
         if (cudaMemcpy(h->coef_buf, host.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) rc = CH_ECUDA;

@@ -279,3 +279,92 @@ inline std::vector<double> warp_tables(const LineFactors& F, int M) {
 }
 
 }  // namespace chg
+
+namespace chg {
+
+// Tables of the column solver (lanes = 32 adjacent lines, warp w = rows
+// [w R, w R + R)): per row (l1, l2, 1/u0, 0), (u1/u0, u2/u0), Woodbury W and Z
+// rows (zero padding past n), then per warp-chunk the forward transfer matrix
+// P_w = A_{b-1} ... A_a and the backward one Q_w = B_a ... B_{b-1}.
+struct ColLayout {
+    size_t fwd, bwd, W, Z, P, Q, S, total;
+};
+
+inline ColLayout col_layout(int nw, int R) {
+    ColLayout L;
+    const size_t rows = (size_t)nw * R;
+    size_t off = 0;
+    L.fwd = off; off += rows * 4;
+    L.bwd = off; off += rows * 2;
+    L.W = off;   off += rows * 4;
+    L.Z = off;   off += rows * 4;
+    L.P = off;   off += (size_t)nw * 4;
+    L.Q = off;   off += (size_t)nw * 4;
+    L.S = off;   off += 16;
+    L.total = (off + 63) / 64 * 64;
+    return L;
+}
+
+inline std::vector<double> col_tables(const LineFactors& F, int nw, int R) {
+    const ColLayout L = col_layout(nw, R);
+    std::vector<double> t(L.total, 0.0);
+    const int n = F.n;
+    for (int j = 0; j < n; ++j) {
+        t[L.fwd + 4 * (size_t)j + 0] = F.l1[j];
+        t[L.fwd + 4 * (size_t)j + 1] = F.l2[j];
+        t[L.fwd + 4 * (size_t)j + 2] = F.dinv[j];
+        t[L.bwd + 2 * (size_t)j + 0] = F.u1s[j];
+        t[L.bwd + 2 * (size_t)j + 1] = F.u2s[j];
+        if (F.periodic)
+            for (int m = 0; m < 4; ++m) {
+                t[L.W + 4 * (size_t)j + m] = F.W[(size_t)j * 4 + m];
+                t[L.Z + 4 * (size_t)j + m] = F.Z[(size_t)j * 4 + m];
+            }
+    }
+    for (int w = 0; w < nw; ++w) {
+        double p[4] = {1, 0, 0, 1}, q[4] = {1, 0, 0, 1};
+        for (int i = 0; i < R; ++i) {
+            const int j = w * R + i;
+            const double A[4] = {j < n ? -F.l1[j] : 0.0, j < n ? -F.l2[j] : 0.0, 1.0, 0.0};
+            mat2_mul(A, p, p);
+        }
+        for (int i = R - 1; i >= 0; --i) {
+            const int j = w * R + i;
+            const double B[4] = {j < n ? -F.u1s[j] : 0.0, j < n ? -F.u2s[j] : 0.0, 1.0, 0.0};
+            mat2_mul(B, q, q);
+        }
+        for (int m = 0; m < 4; ++m) {
+            t[L.P + 4 * (size_t)w + m] = p[m];
+            t[L.Q + 4 * (size_t)w + m] = q[m];
+        }
+    }
+    if (F.periodic)
+        for (int m = 0; m < 16; ++m) t[L.S + m] = F.S[m];
+    return t;
+}
+
+// Column-solver shape for a line of n cells: nw warps of R rows (powers of
+// two; R <= 16 keeps a warp's rows in registers at full occupancy).  Returns
+// false for lines longer than 512.
+inline bool col_shape(int n, int* nw, int* R) {
+    if (n <= 128) {
+        int r = 1;
+        while (8 * r < n) r *= 2;
+        *nw = 8;
+        *R = r;
+        return true;
+    }
+    if (n <= 256) {
+        *nw = 16;
+        *R = 16;
+        return true;
+    }
+    if (n <= 512) {
+        *nw = 32;
+        *R = 16;
+        return true;
+    }
+    return false;
+}
+
+}  // namespace chg

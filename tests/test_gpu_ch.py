@@ -220,3 +220,18 @@ def test_graph_replay_matches_direct_launches():
         s.set_velocity_fine(*f["vel"])
         s.step(5)
     assert np.array_equal(a.field(), b.field())
+
+
+@pytest.mark.parametrize("shape,bc", [((6, 600, 8), (co.PERIODIC, co.PERIODIC, co.NOFLUX)),
+                                      ((560, 5, 6), (co.NOFLUX, co.NOFLUX, co.PERIODIC))])
+def test_fp32_long_lines_use_the_tile_solver(shape, bc):
+    """Lines longer than 512 cells take the shared-memory tile solver."""
+    h = 1.0 / 64
+    cn = 0.75 * h
+    rng = np.random.default_rng(17)
+    C0 = 0.5 + 0.2 * rng.standard_normal(shape)
+    dt = 2e-4
+    s = make(shape, h, bc, cn, 50.0, dt, C0, "f32")
+    s.step(3)
+    ref = co.step(C0, None, oracle_params(shape, h, bc, cn, 50.0, dt), 3)
+    assert rel_l2(s.field(), ref) <= 1e-6
