@@ -75,7 +75,8 @@ typedef struct ch_params {
     int32_t reserved;     /* must be 0 */
     /* optional coarse (Navier-Stokes) mesh for the velocity transfer; all 0/NULL if unused.
      * Host arrays of face coordinates, read during ch_create only: xf has ncx+1 entries,
-     * starting at 0 and ending at nx*h (likewise y, z).  Any (stretched) spacing. */
+     * starting at 0 and ending at nx*h (likewise y, z).  Any (stretched) spacing;
+     * 4 to 2048 coarse cells per direction. */
     int64_t ncx, ncy, ncz;
     const double* xf_coarse;
     const double* yf_coarse;
@@ -95,8 +96,8 @@ size_t ch_workspace_bytes(const ch_params* p);
  * work: device workspace of >= ch_workspace_bytes(p) bytes, 256-byte aligned.
  * stream: cudaStream_t for all work.  Builds the LU factors of the line
  * operators (I + (alpha_l dt M / 2) A_d) for the three RK3 substeps, and with
- * a coarse mesh the Hermite index/weight tables (Sec. 3.4: "generated only
- * once").  Errors: CH_EINVAL (sizes < 5, non-positive h/cn/pe/dt/w, bad bc,
+ * a coarse mesh the Hermite index/weight tables (Sec. 3.4: the tables are built
+ * once per mesh pair).  Errors: CH_EINVAL (sizes < 5, non-positive h/cn/pe/dt/w, bad bc,
  * coarse faces not spanning the fine box, misaligned pointers), CH_ENOMEM,
  * CH_ECUDA.  On success *out owns the tables until ch_free. */
 int ch_create(const ch_params* p, void* C, void* work, size_t work_bytes, void* stream, ch_handle** out);

@@ -112,6 +112,9 @@ __device__ __forceinline__ void yz_item(const BoxDesc& B, int tile, int l, float
                                                tile, smem);
 }
 
+// MAXM: the largest rows-per-lane of any box (4 or 8); smaller builds carry
+// fewer solver variants and fewer registers.
+template <int MAXM>
 __device__ void run_phase(const BatchArgs& A, int ph, int l, float* smem) {
     const int n = A.nitems[ph];
     const int4* items = A.items[ph];
@@ -126,7 +129,7 @@ __device__ void run_phase(const BatchArgs& A, int ph, int l, float* smem) {
                 case 1: x_item<1>(B, w.y, l); break;
                 case 2: x_item<2>(B, w.y, l); break;
                 case 4: x_item<4>(B, w.y, l); break;
-                default: x_item<8>(B, w.y, l); break;
+                default: x_item<MAXM>(B, w.y, l); break;
             }
         } else {
             const int m = B.M[ph - 1];
@@ -135,14 +138,14 @@ __device__ void run_phase(const BatchArgs& A, int ph, int l, float* smem) {
                     case 1: yz_item<1, false>(B, w.y, l, smem, A.status); break;
                     case 2: yz_item<2, false>(B, w.y, l, smem, A.status); break;
                     case 4: yz_item<4, false>(B, w.y, l, smem, A.status); break;
-                    default: yz_item<8, false>(B, w.y, l, smem, A.status); break;
+                    default: yz_item<MAXM, false>(B, w.y, l, smem, A.status); break;
                 }
             } else {
                 switch (m) {
                     case 1: yz_item<1, true>(B, w.y, l, smem, A.status); break;
                     case 2: yz_item<2, true>(B, w.y, l, smem, A.status); break;
                     case 4: yz_item<4, true>(B, w.y, l, smem, A.status); break;
-                    default: yz_item<8, true>(B, w.y, l, smem, A.status); break;
+                    default: yz_item<MAXM, true>(B, w.y, l, smem, A.status); break;
                 }
             }
         }
@@ -150,21 +153,25 @@ __device__ void run_phase(const BatchArgs& A, int ph, int l, float* smem) {
 }
 
 // One full RK3 step of every box in one cooperative launch.
-__global__ void __launch_bounds__(kBThreads, 2) ch_batch_persistent(BatchArgs A) {
+template <int MAXM>
+__global__ void __launch_bounds__(kBThreads, 3) ch_batch_persistent(BatchArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* smem = reinterpret_cast<float*>(smem_raw);
     for (int l = 0; l < kRK; ++l)
         for (int ph = 0; ph < 4; ++ph) {
-            run_phase(A, ph, l, smem);
+            run_phase<MAXM>(A, ph, l, smem);
             if (l == kRK - 1 && ph == 3) break;
             if (!grid_barrier(A)) return;
         }
 }
 
-// One phase of one substep for every box.
-__global__ void __launch_bounds__(kBThreads, 2) ch_batch_phase(BatchArgs A, int ph, int l) {
+// One phase of one substep for every box, specialised per phase so that each
+// phase gets its own register allocation (the persistent kernel must carry
+// the largest of all phases).
+template <int PH, int MAXM>
+__global__ void __launch_bounds__(kBThreads) ch_batch_phase(BatchArgs A, int l) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    run_phase(A, ph, l, reinterpret_cast<float*>(smem_raw));
+    run_phase<MAXM>(A, PH, l, reinterpret_cast<float*>(smem_raw));
 }
 
 // FP64 mass of every box: blockIdx.y = box.
@@ -234,6 +241,7 @@ struct ch_batch {
     int grid = 0;
     size_t smem = 0;
     int num_sms = 0;
+    int max_m = 1;  // largest rows-per-lane of the warp solver over all boxes
     cudaGraphExec_t graph = nullptr;
     bool graph_ready = false;
     char err[512] = {0};
@@ -308,7 +316,8 @@ BatchArgs batch_args(const ch_batch* b) {
     return A;
 }
 
-int launch_step(ch_batch* b) {
+template <int MAXM>
+int launch_step_m(ch_batch* b) {
     const BatchArgs A = batch_args(b);
     if (b->mode == 0) {
         cudaLaunchConfig_t cfg = {};
@@ -321,15 +330,35 @@ int launch_step(ch_batch* b) {
         attr[0].val.cooperative = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        CHB_CUDA(b, cudaLaunchKernelEx(&cfg, ch_batch_persistent, A));
+        CHB_CUDA(b, cudaLaunchKernelEx(&cfg, ch_batch_persistent<MAXM>, A));
     } else {
         for (int l = 0; l < kRK; ++l)
             for (int ph = 0; ph < 4; ++ph) {
-                const unsigned g = (unsigned)std::max(1, std::min(b->nitems[ph], b->grid * 4));
-                ch_batch_phase<<<g, kBThreads, b->smem, b->stream>>>(A, ph, l);
+                // one CTA per item: the phase kernels hold no barrier
+                const unsigned g = (unsigned)std::max(1, b->nitems[ph]);
+                switch (ph) {
+                    case 0: ch_batch_phase<0, MAXM><<<g, kBThreads, b->smem, b->stream>>>(A, l); break;
+                    case 1: ch_batch_phase<1, MAXM><<<g, kBThreads, b->smem, b->stream>>>(A, l); break;
+                    case 2: ch_batch_phase<2, MAXM><<<g, kBThreads, b->smem, b->stream>>>(A, l); break;
+                    default: ch_batch_phase<3, MAXM><<<g, kBThreads, b->smem, b->stream>>>(A, l); break;
+                }
                 CHB_CUDA(b, cudaGetLastError());
             }
     }
+    return CH_OK;
+}
+
+int launch_step(ch_batch* b) { return b->max_m <= 4 ? launch_step_m<4>(b) : launch_step_m<8>(b); }
+
+template <int MAXM>
+int set_attrs_batch(ch_batch* b, int* maxb) {
+    CHB_CUDA(b, cudaFuncSetAttribute(ch_batch_persistent<MAXM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)b->smem));
+    CHB_CUDA(b, cudaFuncSetAttribute(ch_batch_phase<0, MAXM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+    CHB_CUDA(b, cudaFuncSetAttribute(ch_batch_phase<1, MAXM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+    CHB_CUDA(b, cudaFuncSetAttribute(ch_batch_phase<2, MAXM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+    CHB_CUDA(b, cudaFuncSetAttribute(ch_batch_phase<3, MAXM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+    CHB_CUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(maxb, ch_batch_persistent<MAXM>, kBThreads, b->smem));
     return CH_OK;
 }
 
@@ -341,9 +370,8 @@ int configure(ch_batch* b) {
     int rc = build_items(b);
     if (rc != CH_OK) return rc;
     int maxb = 0;
-    CHB_CUDA(b, cudaFuncSetAttribute(ch_batch_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
-    CHB_CUDA(b, cudaFuncSetAttribute(ch_batch_phase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
-    CHB_CUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxb, ch_batch_persistent, kBThreads, b->smem));
+    rc = b->max_m <= 4 ? set_attrs_batch<4>(b, &maxb) : set_attrs_batch<8>(b, &maxb);
+    if (rc != CH_OK) return rc;
     if (maxb < 1) return bfail(b, CH_EINVAL, "batch kernel does not fit on an SM");
     b->blocks_per_sm = std::max(1, std::min(b->blocks_per_sm, maxb));
     b->grid = b->blocks_per_sm * b->num_sms;
@@ -437,6 +465,7 @@ int ch_batch_create(const ch_params* boxes, int nbox, void* const* C, void* work
         }
     }
     b->smem = (size_t)32 * maxM * 32 * sizeof(float);
+    b->max_m = maxM;
     int rc = CH_OK;
     if (cudaMalloc(&b->coef_buf, coef_total) != cudaSuccess) rc = CH_ENOMEM;
     if (rc == CH_OK) {
@@ -621,7 +650,8 @@ int ch_batch_autotune(ch_batch* b, int steps_per_trial, char* report, size_t rep
     for (int mode = 0; mode < 2; ++mode)
         for (int bpsm : {1, 2, 3})
             for (int zc : {4, 8, 16})
-                for (int lpt : {0, 1}) cands.push_back({mode, bpsm, zc, lpt});
+                for (int lpt : {0, 1})
+                    if (mode == 0 || bpsm == 1) cands.push_back({mode, bpsm, zc, lpt});
     std::string rep;
     double best = 1e30;
     Cand bc = {b->mode, b->blocks_per_sm, b->zchunk, b->lpt};

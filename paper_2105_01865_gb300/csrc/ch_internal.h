@@ -13,6 +13,7 @@
 namespace chg {
 
 constexpr int kRK = 3;  // RK3 substeps (Sec. 3)
+constexpr int kMaxCoarseLine = 2048;  // coarse cells per direction (one x-line per warp in shared memory)
 
 // Low-storage RK3 coefficients (Sec. 3 cites the scheme without printing it):
 // gamma, rho per substep; alpha = gamma + rho weights the Crank-Nicolson step.

@@ -117,36 +117,6 @@ struct Tab {
     const T* __restrict__ w;
 };
 
-// Step (2): the 64-point tri-cubic Hermite value of a coarse cell-centred
-// field at fine cell (i, j, k), contracted x first, then y, then z.
-template <typename T>
-__device__ __forceinline__ T hermite3(const T* __restrict__ G, int ncx, int ncy, int ncz, int sx, const T* wx,
-                                      int sy, const T* wy, int sz, const T* wz) {
-    T acc = T(0);
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        int kz = sz + c;
-        kz -= (kz >= ncz) ? ncz : 0;
-        T accy = T(0);
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            int ky = sy + b;
-            ky -= (ky >= ncy) ? ncy : 0;
-            const T* row = G + ((int64_t)kz * ncy + ky) * ncx;
-            T accx = T(0);
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                int kx = sx + a;
-                kx -= (kx >= ncx) ? ncx : 0;
-                accx += wx[a] * row[kx];
-            }
-            accy += wy[b] * accx;
-        }
-        acc += wz[c] * accy;
-    }
-    return acc;
-}
-
 // 2D Hermite of a coarse face plane P[row][col] (row stride `stride`).
 template <typename T>
 __device__ __forceinline__ T hermite2(const T* __restrict__ P, int64_t row_stride, int64_t col_stride, int nr,
@@ -183,100 +153,166 @@ __device__ __forceinline__ void load_w(const T* __restrict__ w, int i, T* out) {
     for (int m = 0; m < 4; ++m) out[m] = w[4 * i + m];
 }
 
-// Step (3) along x: one warp per fine x-line (j, k).  u(face i) = u_ref(j, k)
-// + h sum_{i' < i} Gx(i', j, k), the running sum kept in FP64 (warp scan).
+// Step (3) along x: one warp per fine x-line (j, k).  The 64-point stencil
+// is sum-factorised: the warp first contracts the 16 coarse rows of its (y, z)
+// stencil into one coarse x-line g(ix) = sum_{b,c} wy_b wz_c G(ix, sy+b, sz+c)
+// (coalesced over ix, kept in shared memory), then every fine point needs only
+// its 4-point x-stencil of g.  u(face i) = u_ref(j, k) + h sum_{i' < i} Gx(i'),
+// the running sum kept in FP64 (warp scan with carry).
+constexpr int kMrWarps = 8;
+
 template <typename T>
-__global__ void mr_integrate_x(const T* __restrict__ gx, const T* __restrict__ uc, Tab<T> tx, Tab<T> ty, Tab<T> tz,
-                               MrArgs a, T* __restrict__ u) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (warp >= a.ny * a.nz) return;
+__global__ void __launch_bounds__(kMrWarps * 32)
+mr_integrate_x(const T* __restrict__ gx, const T* __restrict__ uc, Tab<T> tx, Tab<T> ty, Tab<T> tz, MrArgs a,
+               T* __restrict__ u) {
+    extern __shared__ __align__(16) unsigned char mr_smem[];  // kMrWarps coarse lines of ncx values
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = blockIdx.x * kMrWarps + wib;
+    if (warp >= a.ny * a.nz) return;  // whole warp
     const int j = warp % a.ny, k = warp / a.ny;
     T wy[4], wz[4];
     load_w(ty.w, j, wy);
     load_w(tz.w, k, wz);
     const int sy = ty.s[j], sz = tz.s[k];
-    T uref = T(0);
-    if (!a.wall[0]) {
-        // coarse x-face plane 0: uc[kz][ky][0]
-        uref = hermite2(uc, (int64_t)a.ncy * a.ncfx, (int64_t)a.ncfx, a.ncz, a.ncy, sz, wz, sy, wy);
+    T* g = reinterpret_cast<T*>(mr_smem) + (int64_t)wib * a.ncx;
+    for (int ix = lane; ix < a.ncx; ix += 32) {
+        T acc = T(0);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            int kz = sz + c;
+            kz -= (kz >= a.ncz) ? a.ncz : 0;
+            T accy = T(0);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                int ky = sy + b;
+                ky -= (ky >= a.ncy) ? a.ncy : 0;
+                accy += wy[b] * gx[((int64_t)kz * a.ncy + ky) * a.ncx + ix];
+            }
+            acc += wz[c] * accy;
+        }
+        g[ix] = acc;
     }
+    T uref = T(0);
+    if (!a.wall[0]) uref = hermite2(uc, (int64_t)a.ncy * a.ncfx, (int64_t)a.ncfx, a.ncz, a.ncy, sz, wz, sy, wy);
+    __syncwarp();
     T* row = u + ((int64_t)k * a.ny + j) * a.nfx;
     double carry = 0.0;
     for (int i0 = 0; i0 < a.nx; i0 += 32) {
         const int i = i0 + lane;
-        double g = 0.0;
+        double gv = 0.0;
         if (i < a.nx) {
             T wx[4];
             load_w(tx.w, i, wx);
-            g = (double)hermite3(gx, a.ncx, a.ncy, a.ncz, tx.s[i], wx, sy, wy, sz, wz);
+            const int sx = tx.s[i];
+            T acc = T(0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                int kx = sx + q;
+                kx -= (kx >= a.ncx) ? a.ncx : 0;
+                acc += wx[q] * g[kx];
+            }
+            gv = (double)acc;
         }
-        // exclusive prefix sum within the warp
-        double incl = g;
+        double incl = gv;
         for (int o = 1; o < 32; o <<= 1) {
             const double t = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += t;
         }
-        const double excl = carry + incl - g;
+        const double excl = carry + incl - gv;
         if (i < a.nx) row[i] = uref + T(a.h * excl);
         carry += __shfl_sync(0xffffffffu, incl, 31);
     }
     if (a.wall[0] && lane == 0) row[a.nx] = uref + T(a.h * carry);
 }
 
-// Step (3) along y: one thread per fine (i, k), marching j.
+// Contraction of a coarse gradient over the 4 x 4 stencil of the two
+// transverse directions at one coarse index along the marching direction:
+// value(m) = sum_{p,q} wp_p wq_q G(m, sp + p, sq + q) with the index order
+// given by the strides.
 template <typename T>
-__global__ void mr_integrate_y(const T* __restrict__ gy, const T* __restrict__ vc, Tab<T> tx, Tab<T> ty, Tab<T> tz,
-                               MrArgs a, T* __restrict__ v) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)a.nx * a.nz) return;
-    const int i = (int)(t % a.nx), k = (int)(t / a.nx);
-    T wx[4], wz[4];
-    load_w(tx.w, i, wx);
-    load_w(tz.w, k, wz);
-    const int sx = tx.s[i], sz = tz.s[k];
-    T vref = T(0);
-    if (!a.wall[1]) {
-        // coarse y-face plane 0: vc[kz][0][kx]
-        vref = hermite2(vc, (int64_t)a.ncfy * a.ncx, (int64_t)1, a.ncz, a.ncx, sz, wz, sx, wx);
+__device__ __forceinline__ T contract16(const T* __restrict__ G, int64_t off_m, int sp, int np, int64_t stride_p,
+                                        const T* wp, int sq, int nq, int64_t stride_q, const T* wq) {
+    T acc = T(0);
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        int kp = sp + p;
+        kp -= (kp >= np) ? np : 0;
+        T accq = T(0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int kq = sq + q;
+            kq -= (kq >= nq) ? nq : 0;
+            accq += wq[q] * G[off_m + kp * stride_p + kq * stride_q];
+        }
+        acc += wp[p] * accq;
     }
-    double run = 0.0;
-    for (int j = 0; j < a.ny; ++j) {
-        T wy[4];
-        load_w(ty.w, j, wy);
-        const double g = (double)hermite3(gy, a.ncx, a.ncy, a.ncz, sx, wx, ty.s[j], wy, sz, wz);
-        v[((int64_t)k * a.nfy + j) * a.nx + i] = vref + T(a.h * run);
-        run += g;
-    }
-    if (a.wall[1]) v[((int64_t)k * a.nfy + a.ny) * a.nx + i] = vref + T(a.h * run);
+    return acc;
 }
 
-// Step (3) along z: one thread per fine (i, j), marching k.  With walls the
-// reference plane is the bottom wall (w = 0).
-template <typename T>
-__global__ void mr_integrate_z(const T* __restrict__ gz, const T* __restrict__ wc, Tab<T> tx, Tab<T> ty, Tab<T> tz,
-                               MrArgs a, T* __restrict__ w) {
+// Steps (2)-(3) along a strided direction (y: v, or z: w): one thread per
+// fine transverse position, marching the fine line.  The transverse 16-point
+// contraction of each coarse index along the line is computed once and kept
+// in a 4-entry window that slides with the fine point's stencil, so a fine
+// point costs 4 FMAs instead of 64 gathers.
+template <typename T, int DIR>
+__global__ void __launch_bounds__(256)
+mr_integrate_yz(const T* __restrict__ G, const T* __restrict__ Vc, Tab<T> tx, Tab<T> ty, Tab<T> tz, MrArgs a,
+                T* __restrict__ out) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)a.nx * a.ny) return;
-    const int i = (int)(t % a.nx), j = (int)(t / a.nx);
-    T wx[4], wy[4];
-    load_w(tx.w, i, wx);
-    load_w(ty.w, j, wy);
-    const int sx = tx.s[i], sy = ty.s[j];
-    T wref = T(0);
-    if (!a.wall[2]) {
-        // coarse z-face plane 0: wc[0][ky][kx]
-        wref = hermite2(wc, (int64_t)a.ncx, (int64_t)1, a.ncy, a.ncx, sy, wy, sx, wx);
+    const int nlong = DIR == 1 ? a.ny : a.nz;                 // fine cells along the line
+    const int ntr = DIR == 1 ? a.nz : a.ny;                   // second transverse fine size
+    if (t >= (int64_t)a.nx * ntr) return;
+    const int i = (int)(t % a.nx), o = (int)(t / a.nx);       // fine x and the other transverse index
+    T wxv[4], wov[4];
+    load_w(tx.w, i, wxv);
+    const Tab<T>& to = DIR == 1 ? tz : ty;                    // table of the other transverse direction
+    const Tab<T>& tl = DIR == 1 ? ty : tz;                    // table along the line
+    load_w(to.w, o, wov);
+    const int sx = tx.s[i], so = to.s[o];
+    const int ncl = DIR == 1 ? a.ncy : a.ncz;                 // coarse cells along the line
+    const int nco = DIR == 1 ? a.ncz : a.ncy;                 // coarse cells of the other transverse dir
+    // strides of G[kz][ky][kx]
+    const int64_t st_l = DIR == 1 ? (int64_t)a.ncx : (int64_t)a.ncx * a.ncy;
+    const int64_t st_o = DIR == 1 ? (int64_t)a.ncx * a.ncy : (int64_t)a.ncx;
+    // reference plane: v at y = 0 (plane [kz][0][kx] of Vc) or w at z = 0
+    T ref = T(0);
+    if (!a.wall[DIR]) {
+        if (DIR == 1)
+            ref = hermite2(Vc, (int64_t)a.ncfy * a.ncx, (int64_t)1, a.ncz, a.ncx, so, wov, sx, wxv);
+        else
+            ref = hermite2(Vc, (int64_t)a.ncx, (int64_t)1, a.ncy, a.ncx, so, wov, sx, wxv);
     }
+    T win[4];
+    int ws = -1;  // coarse start index of the window
     double run = 0.0;
-    const int64_t plane = (int64_t)a.nx * a.ny;
-    for (int k = 0; k < a.nz; ++k) {
-        T wz[4];
-        load_w(tz.w, k, wz);
-        const double g = (double)hermite3(gz, a.ncx, a.ncy, a.ncz, sx, wx, sy, wy, tz.s[k], wz);
-        w[(int64_t)k * plane + t] = wref + T(a.h * run);
-        run += g;
+    for (int jl = 0; jl < nlong; ++jl) {
+        const int sl = tl.s[jl];
+        if (sl != ws) {
+            int first = 0;
+            if (ws >= 0 && sl == (ws + 1 == ncl ? 0 : ws + 1)) {
+                win[0] = win[1];
+                win[1] = win[2];
+                win[2] = win[3];
+                first = 3;
+            }
+            for (int m = first; m < 4; ++m) {
+                int km = sl + m;
+                km -= (km >= ncl) ? ncl : 0;
+                win[m] = contract16(G, km * st_l, so, nco, st_o, wov, sx, a.ncx, (int64_t)1, wxv);
+            }
+            ws = sl;
+        }
+        T wl[4];
+        load_w(tl.w, jl, wl);
+        const double gval = (double)(wl[0] * win[0] + wl[1] * win[1] + wl[2] * win[2] + wl[3] * win[3]);
+        const int64_t idx = DIR == 1 ? ((int64_t)o * a.nfy + jl) * a.nx + i : ((int64_t)jl * a.ny + o) * a.nx + i;
+        out[idx] = ref + T(a.h * run);
+        run += gval;
     }
-    if (a.wall[2]) w[(int64_t)a.nz * plane + t] = wref + T(a.h * run);
+    if (a.wall[DIR]) {
+        const int64_t idx = DIR == 1 ? ((int64_t)o * a.nfy + a.ny) * a.nx + i : ((int64_t)a.nz * a.ny + o) * a.nx + i;
+        out[idx] = ref + T(a.h * run);
+    }
 }
 
 MrArgs mr_args(const ch_handle* h) {
@@ -321,20 +357,27 @@ int interp(ch_handle* h) {
     const Tab<T> tx = tab<T>(h, 0), ty = tab<T>(h, 1), tz = tab<T>(h, 2);
     {
         const int64_t warps = (int64_t)a.ny * a.nz;
-        const unsigned blocks = (unsigned)((warps * 32 + kThreads - 1) / kThreads);
-        mr_integrate_x<T><<<blocks, kThreads, 0, h->stream>>>((const T*)h->grad_c[0], (const T*)h->vel_c[0], tx, ty,
-                                                              tz, a, (T*)h->vel[0]);
+        const unsigned blocks = (unsigned)((warps + kMrWarps - 1) / kMrWarps);
+        const size_t smem = (size_t)kMrWarps * a.ncx * sizeof(T);
+        static bool attr_set = false;  // one instantiation per T
+        if (!attr_set) {
+            CHG_CUDA(h, cudaFuncSetAttribute(mr_integrate_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(kMrWarps * kMaxCoarseLine * sizeof(T))));
+            attr_set = true;
+        }
+        mr_integrate_x<T><<<blocks, kMrWarps * 32, smem, h->stream>>>((const T*)h->grad_c[0], (const T*)h->vel_c[0], tx,
+                                                                   ty, tz, a, (T*)h->vel[0]);
         CHG_CUDA(h, cudaGetLastError());
     }
     {
         const int64_t thr = (int64_t)a.nx * a.nz;
-        mr_integrate_y<T><<<(unsigned)((thr + kThreads - 1) / kThreads), kThreads, 0, h->stream>>>(
+        mr_integrate_yz<T, 1><<<(unsigned)((thr + 255) / 256), 256, 0, h->stream>>>(
             (const T*)h->grad_c[1], (const T*)h->vel_c[1], tx, ty, tz, a, (T*)h->vel[1]);
         CHG_CUDA(h, cudaGetLastError());
     }
     {
         const int64_t thr = (int64_t)a.nx * a.ny;
-        mr_integrate_z<T><<<(unsigned)((thr + kThreads - 1) / kThreads), kThreads, 0, h->stream>>>(
+        mr_integrate_yz<T, 2><<<(unsigned)((thr + 255) / 256), 256, 0, h->stream>>>(
             (const T*)h->grad_c[2], (const T*)h->vel_c[2], tx, ty, tz, a, (T*)h->vel[2]);
         CHG_CUDA(h, cudaGetLastError());
     }

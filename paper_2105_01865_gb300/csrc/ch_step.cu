@@ -46,6 +46,8 @@ bool params_valid(const ch_params* p, char* why, size_t wl) {
     const bool any_c = p->ncx || p->ncy || p->ncz || p->xf_coarse || p->yf_coarse || p->zf_coarse;
     if (any_c) {
         if (p->ncx < 4 || p->ncy < 4 || p->ncz < 4) return bad("coarse mesh needs >= 4 cells per direction");
+        if (p->ncx > kMaxCoarseLine || p->ncy > kMaxCoarseLine || p->ncz > kMaxCoarseLine)
+            return bad("coarse mesh has more than 2048 cells in a direction");
         if (!p->xf_coarse || !p->yf_coarse || !p->zf_coarse) return bad("coarse face coordinates missing");
         if (!p->advect) return bad("a coarse mesh requires advect = 1");
         const int64_t nf[3] = {p->nx, p->ny, p->nz};
