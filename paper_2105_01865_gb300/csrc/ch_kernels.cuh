@@ -352,160 +352,262 @@ __device__ __forceinline__ void ld2(const double* p, double& a, double& b) {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// Solve the line whose rows lane*M .. lane*M+M-1 are in v[] (rhs in, solution out).
-template <typename T, int M>
-__device__ __forceinline__ void warp_line_solve(T (&v)[M], const WCoef<T>& cf, int lane) {
+// Explicitly rounded multiply-adds: the solver's arithmetic is fixed in the
+// source, so every kernel that inlines it (standalone, batched persistent,
+// batched per phase) rounds identically and the results agree bit for bit.
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double fmul(double a, double b) { return __dmul_rn(a, b); }
+
+// r . a for a 4-vector row r, as an explicit multiply-add chain
+template <typename T>
+__device__ __forceinline__ T dot4(const V4<T>& r, const T (&a)[4]) {
+    return fmadd(r.x, a[0], fmadd(r.y, a[1], fmadd(r.z, a[2], fmul(r.w, a[3]))));
+}
+
+// Solve L lines of the same operator together; line q's rows lane*M ..
+// lane*M+M-1 are in v[q][] (rhs in, solution out).  Every coefficient load
+// serves the L lines, and their L recurrences are independent chains.
+template <typename T, int M, int L>
+__device__ __forceinline__ void warp_lines_solve(T (&v)[L][M], const WCoef<T>& cf, int lane) {
     const bool per = cf.periodic;
     // ---- forward elimination: zero-start pass over the chunk
-    T y1 = T(0), y2 = T(0);
-    T acc0 = T(0), acc1 = T(0), acc2 = T(0), acc3 = T(0);
+    T y1[L], y2[L], acc[L][4];
+#pragma unroll
+    for (int q = 0; q < L; ++q) {
+        y1[q] = y2[q] = T(0);
+        acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = T(0);
+    }
 #pragma unroll
     for (int i = 0; i < M; ++i) {
         const V4<T> c = ld4(cf.fwd + (i * 32 + lane) * 4);
-        const T y = (v[i] - c.y * y2) - c.x * y1;
-        y2 = y1;
-        y1 = y;
+#pragma unroll
+        for (int q = 0; q < L; ++q) {
+            const T y = fmadd(-c.x, y1[q], fmadd(-c.y, y2[q], v[q][i]));
+            y2[q] = y1[q];
+            y1[q] = y;
+        }
         if (per) {
             const V4<T> w = ld4(cf.W + (i * 32 + lane) * 4);
-            acc0 += w.x * v[i];
-            acc1 += w.y * v[i];
-            acc2 += w.z * v[i];
-            acc3 += w.w * v[i];
+#pragma unroll
+            for (int q = 0; q < L; ++q) {
+                acc[q][0] = fmadd(w.x, v[q][i], acc[q][0]);
+                acc[q][1] = fmadd(w.y, v[q][i], acc[q][1]);
+                acc[q][2] = fmadd(w.z, v[q][i], acc[q][2]);
+                acc[q][3] = fmadd(w.w, v[q][i], acc[q][3]);
+            }
         }
     }
     // inclusive scan of the chunk end states over lanes 0..lane
-    T q0 = y1, q1 = y2;
+    T q0[L], q1[L];
+#pragma unroll
+    for (int q = 0; q < L; ++q) {
+        q0[q] = y1[q];
+        q1[q] = y2[q];
+    }
 #pragma unroll
     for (int s = 0; s < 5; ++s) {
         const int d = 1 << s;
-        const T o0 = __shfl_up_sync(kFull, q0, d), o1 = __shfl_up_sync(kFull, q1, d);
+        T o0[L], o1[L];
+#pragma unroll
+        for (int q = 0; q < L; ++q) {
+            o0[q] = __shfl_up_sync(kFull, q0[q], d);
+            o1[q] = __shfl_up_sync(kFull, q1[q], d);
+        }
         if (lane >= d) {
             const V4<T> P = ld4(cf.Pf + (s * 32 + lane) * 4);
-            q0 += P.x * o0 + P.y * o1;
-            q1 += P.z * o0 + P.w * o1;
+#pragma unroll
+            for (int q = 0; q < L; ++q) {
+                q0[q] = fmadd(P.x, o0[q], fmadd(P.y, o1[q], q0[q]));
+                q1[q] = fmadd(P.z, o0[q], fmadd(P.w, o1[q], q1[q]));
+            }
         }
     }
-    y1 = __shfl_up_sync(kFull, q0, 1);
-    y2 = __shfl_up_sync(kFull, q1, 1);
-    if (lane == 0) y1 = y2 = T(0);
+#pragma unroll
+    for (int q = 0; q < L; ++q) {
+        y1[q] = __shfl_up_sync(kFull, q0[q], 1);
+        y2[q] = __shfl_up_sync(kFull, q1[q], 1);
+        if (lane == 0) y1[q] = y2[q] = T(0);
+    }
 #pragma unroll
     for (int i = 0; i < M; ++i) {
         const V4<T> c = ld4(cf.fwd + (i * 32 + lane) * 4);
-        const T y = (v[i] - c.y * y2) - c.x * y1;
-        y2 = y1;
-        y1 = y;
-        v[i] = y * c.z;
+#pragma unroll
+        for (int q = 0; q < L; ++q) {
+            const T y = fmadd(-c.x, y1[q], fmadd(-c.y, y2[q], v[q][i]));
+            y2[q] = y1[q];
+            y1[q] = y;
+            v[q][i] = fmul(y, c.z);
+        }
     }
     // ---- Woodbury right-hand side s = S W^T r (warp reduction)
-    T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+    T sv[L][4];
+#pragma unroll
+    for (int q = 0; q < L; ++q) sv[q][0] = sv[q][1] = sv[q][2] = sv[q][3] = T(0);
     if (per) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            acc0 += __shfl_xor_sync(kFull, acc0, o);
-            acc1 += __shfl_xor_sync(kFull, acc1, o);
-            acc2 += __shfl_xor_sync(kFull, acc2, o);
-            acc3 += __shfl_xor_sync(kFull, acc3, o);
-        }
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < L; ++q)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[q][e] += __shfl_xor_sync(kFull, acc[q][e], o);
         const V4<T> r0 = ld4(cf.S), r1 = ld4(cf.S + 4), r2 = ld4(cf.S + 8), r3 = ld4(cf.S + 12);
-        s0 = r0.x * acc0 + r0.y * acc1 + r0.z * acc2 + r0.w * acc3;
-        s1 = r1.x * acc0 + r1.y * acc1 + r1.z * acc2 + r1.w * acc3;
-        s2 = r2.x * acc0 + r2.y * acc1 + r2.z * acc2 + r2.w * acc3;
-        s3 = r3.x * acc0 + r3.y * acc1 + r3.z * acc2 + r3.w * acc3;
+#pragma unroll
+        for (int q = 0; q < L; ++q) {
+            sv[q][0] = dot4(r0, acc[q]);
+            sv[q][1] = dot4(r1, acc[q]);
+            sv[q][2] = dot4(r2, acc[q]);
+            sv[q][3] = dot4(r3, acc[q]);
+        }
     }
     // ---- back substitution: zero-start pass over the chunk (bottom row first)
-    T x1 = T(0), x2 = T(0);
+    T x1[L], x2[L];
+#pragma unroll
+    for (int q = 0; q < L; ++q) x1[q] = x2[q] = T(0);
 #pragma unroll
     for (int i = M - 1; i >= 0; --i) {
         T u1, u2;
         ld2(cf.bwd + (i * 32 + lane) * 2, u1, u2);
-        const T x = (v[i] - u2 * x2) - u1 * x1;
-        x2 = x1;
-        x1 = x;
+#pragma unroll
+        for (int q = 0; q < L; ++q) {
+            const T x = fmadd(-u1, x1[q], fmadd(-u2, x2[q], v[q][i]));
+            x2[q] = x1[q];
+            x1[q] = x;
+        }
     }
     // inclusive scan from the last lane down
-    q0 = x1;
-    q1 = x2;
+#pragma unroll
+    for (int q = 0; q < L; ++q) {
+        q0[q] = x1[q];
+        q1[q] = x2[q];
+    }
 #pragma unroll
     for (int s = 0; s < 5; ++s) {
         const int d = 1 << s;
-        const T o0 = __shfl_down_sync(kFull, q0, d), o1 = __shfl_down_sync(kFull, q1, d);
+        T o0[L], o1[L];
+#pragma unroll
+        for (int q = 0; q < L; ++q) {
+            o0[q] = __shfl_down_sync(kFull, q0[q], d);
+            o1[q] = __shfl_down_sync(kFull, q1[q], d);
+        }
         if (lane + d < 32) {
             const V4<T> P = ld4(cf.Pb + (s * 32 + lane) * 4);
-            q0 += P.x * o0 + P.y * o1;
-            q1 += P.z * o0 + P.w * o1;
+#pragma unroll
+            for (int q = 0; q < L; ++q) {
+                q0[q] = fmadd(P.x, o0[q], fmadd(P.y, o1[q], q0[q]));
+                q1[q] = fmadd(P.z, o0[q], fmadd(P.w, o1[q], q1[q]));
+            }
         }
     }
-    x1 = __shfl_down_sync(kFull, q0, 1);
-    x2 = __shfl_down_sync(kFull, q1, 1);
-    if (lane == 31) x1 = x2 = T(0);
+#pragma unroll
+    for (int q = 0; q < L; ++q) {
+        x1[q] = __shfl_down_sync(kFull, q0[q], 1);
+        x2[q] = __shfl_down_sync(kFull, q1[q], 1);
+        if (lane == 31) x1[q] = x2[q] = T(0);
+    }
 #pragma unroll
     for (int i = M - 1; i >= 0; --i) {
         T u1, u2;
         ld2(cf.bwd + (i * 32 + lane) * 2, u1, u2);
-        const T x = (v[i] - u2 * x2) - u1 * x1;
-        x2 = x1;
-        x1 = x;
-        T o = x;
-        if (per) {
-            const V4<T> z = ld4(cf.Z + (i * 32 + lane) * 4);
-            o -= z.x * s0 + z.y * s1 + z.z * s2 + z.w * s3;
+        V4<T> z = {T(0), T(0), T(0), T(0)};
+        if (per) z = ld4(cf.Z + (i * 32 + lane) * 4);
+#pragma unroll
+        for (int q = 0; q < L; ++q) {
+            const T x = fmadd(-u1, x1[q], fmadd(-u2, x2[q], v[q][i]));
+            x2[q] = x1[q];
+            x1[q] = x;
+            T o = x;
+            if (per) o = fmadd(-z.x, sv[q][0], fmadd(-z.y, sv[q][1], fmadd(-z.z, sv[q][2], fmadd(-z.w, sv[q][3], o))));
+            v[q][i] = o;
         }
-        v[i] = o;
     }
 }
 
-// x-lines (contiguous): one warp per line, lane chunks read and written
-// directly (16-byte vectors when the line and chunk are aligned).
+// One line: rows lane*M .. lane*M+M-1 in v[].
 template <typename T, int M>
-__device__ __forceinline__ void solve_x_line(T* a, int64_t line, int nx, const WCoef<T>& cf) {
+__device__ __forceinline__ void warp_line_solve(T (&v)[M], const WCoef<T>& cf, int lane) {
+    warp_lines_solve<T, M, 1>(*reinterpret_cast<T(*)[1][M]>(&v), cf, lane);
+}
+
+// Lines solved together per warp: CH_SOLVE_LINES (default 2) while a lane
+// holds at most 32 bytes of rows, else one.
+#ifndef CH_SOLVE_LINES
+#define CH_SOLVE_LINES 2
+#endif
+template <typename T, int M>
+struct LinesPerWarp {
+    static constexpr int value = M * sizeof(T) <= 32 ? CH_SOLVE_LINES : 1;
+};
+
+// x-lines (contiguous): one warp per L consecutive lines, lane chunks read
+// and written directly (16-byte vectors when the line and chunk are aligned).
+// Lines at or past nlines are solved on zeros and not stored.
+template <typename T, int M, int L>
+__device__ __forceinline__ void solve_x_lines(T* a, int64_t line0, int64_t nlines, int nx, const WCoef<T>& cf) {
     const int lane = threadIdx.x & 31;
-    T* p = a + line * nx;
     const int j0 = lane * M;
-    T v[M];
+    T v[L][M];
     constexpr int VEC = 16 / sizeof(T);
     const bool vec = (M % VEC == 0) && (nx % VEC == 0) && (j0 + M <= nx);
-    if (vec) {
 #pragma unroll
-        for (int i = 0; i < M; i += VEC) {
-            if (sizeof(T) == 4) {
-                const float4 t = *reinterpret_cast<const float4*>(p + j0 + i);
-                v[i] = (T)t.x; v[i + 1] = (T)t.y; v[i + 2] = (T)t.z; v[i + 3] = (T)t.w;
-            } else {
-                const double2 t = *reinterpret_cast<const double2*>(p + j0 + i);
-                v[i] = (T)t.x; v[i + 1] = (T)t.y;
+    for (int q = 0; q < L; ++q) {
+        const bool live = line0 + q < nlines;
+        const T* p = a + (line0 + q) * nx;
+        if (vec && live) {
+#pragma unroll
+            for (int i = 0; i < M; i += VEC) {
+                if (sizeof(T) == 4) {
+                    const float4 t = *reinterpret_cast<const float4*>(p + j0 + i);
+                    v[q][i] = (T)t.x; v[q][i + 1] = (T)t.y; v[q][i + 2] = (T)t.z; v[q][i + 3] = (T)t.w;
+                } else {
+                    const double2 t = *reinterpret_cast<const double2*>(p + j0 + i);
+                    v[q][i] = (T)t.x; v[q][i + 1] = (T)t.y;
+                }
             }
+        } else {
+#pragma unroll
+            for (int i = 0; i < M; ++i) v[q][i] = (live && j0 + i < nx) ? p[j0 + i] : T(0);
         }
-    } else {
-#pragma unroll
-        for (int i = 0; i < M; ++i) v[i] = (j0 + i < nx) ? p[j0 + i] : T(0);
     }
-    warp_line_solve<T, M>(v, cf, lane);
-    if (vec) {
+    warp_lines_solve<T, M, L>(v, cf, lane);
 #pragma unroll
-        for (int i = 0; i < M; i += VEC) {
-            if (sizeof(T) == 4) {
-                float4 t;
-                t.x = (float)v[i]; t.y = (float)v[i + 1]; t.z = (float)v[i + 2]; t.w = (float)v[i + 3];
-                *reinterpret_cast<float4*>(p + j0 + i) = t;
-            } else {
-                double2 t;
-                t.x = (double)v[i]; t.y = (double)v[i + 1];
-                *reinterpret_cast<double2*>(p + j0 + i) = t;
+    for (int q = 0; q < L; ++q) {
+        if (line0 + q >= nlines) continue;
+        T* p = a + (line0 + q) * nx;
+        if (vec) {
+#pragma unroll
+            for (int i = 0; i < M; i += VEC) {
+                if (sizeof(T) == 4) {
+                    float4 t;
+                    t.x = (float)v[q][i]; t.y = (float)v[q][i + 1]; t.z = (float)v[q][i + 2]; t.w = (float)v[q][i + 3];
+                    *reinterpret_cast<float4*>(p + j0 + i) = t;
+                } else {
+                    double2 t;
+                    t.x = (double)v[q][i]; t.y = (double)v[q][i + 1];
+                    *reinterpret_cast<double2*>(p + j0 + i) = t;
+                }
             }
-        }
-    } else {
+        } else {
 #pragma unroll
-        for (int i = 0; i < M; ++i)
-            if (j0 + i < nx) p[j0 + i] = v[i];
+            for (int i = 0; i < M; ++i)
+                if (j0 + i < nx) p[j0 + i] = v[q][i];
+        }
     }
+}
+
+template <typename T, int M>
+__device__ __forceinline__ void solve_x_line(T* a, int64_t line, int nx, const WCoef<T>& cf) {
+    solve_x_lines<T, M, 1>(a, line, line + 1, nx, cf);
 }
 
 template <typename T, int M>
 __global__ void __launch_bounds__(256)
 ch_solve_x(T* __restrict__ a, int64_t nlines, int nx, WCoef<T> cf) {
-    const int64_t line = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (line >= nlines) return;  // whole warp
-    solve_x_line<T, M>(a, line, nx, cf);
+    constexpr int L = LinesPerWarp<T, M>::value;
+    const int64_t line0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * L;
+    if (line0 >= nlines) return;  // whole warp
+    solve_x_lines<T, M, L>(a, line0, nlines, nx, cf);
 }
 
 // y- or z-lines (strided).  A CTA of 16 warps owns 32 consecutive x of one
@@ -551,14 +653,19 @@ __device__ __forceinline__ void solve_yz_tile(T* a, T* Cf, int nx, int64_t outer
     cp_async_wait<0>();
     __syncthreads();
     const int warp = tid >> 5, lane = tid & 31;
+    constexpr int L = LinesPerWarp<T, M>::value;
 #pragma unroll 1
-    for (int col = warp; col < 32; col += kYZWarps) {
-        T v[M];
+    for (int col = warp * L; col < 32; col += kYZWarps * L) {
+        T v[L][M];
 #pragma unroll
-        for (int i = 0; i < M; ++i) v[i] = s[slot(lane * M + i, col)];
-        warp_line_solve<T, M>(v, cf, lane);
+        for (int q = 0; q < L; ++q)
 #pragma unroll
-        for (int i = 0; i < M; ++i) s[slot(lane * M + i, col)] = v[i];
+            for (int i = 0; i < M; ++i) v[q][i] = s[slot(lane * M + i, col + q)];
+        warp_lines_solve<T, M, L>(v, cf, lane);
+#pragma unroll
+        for (int q = 0; q < L; ++q)
+#pragma unroll
+            for (int i = 0; i < M; ++i) s[slot(lane * M + i, col + q)] = v[q][i];
     }
     __syncthreads();
     bool bad = false;

@@ -134,8 +134,8 @@ int launch_solves_m(ch_handle* h, int l, int dir, T* r, T* Cupd, cudaEvent_t ev_
     const WCoef<T> cf = wcoef<T>(h->lines[dir][l]);
     if (dir == 0) {
         const int64_t nlines = (int64_t)ny * nz;
-        constexpr int wpb = 8;
-        ch_solve_x<T, M><<<(unsigned)((nlines + wpb - 1) / wpb), wpb * 32, 0, h->stream>>>(r, nlines, nx, cf);
+        constexpr int wpb = 8, lpb = wpb * LinesPerWarp<T, M>::value;
+        ch_solve_x<T, M><<<(unsigned)((nlines + lpb - 1) / lpb), wpb * 32, 0, h->stream>>>(r, nlines, nx, cf);
     } else {
         const unsigned xblocks = (unsigned)((nx + 31) / 32);
         const size_t shm = (size_t)32 * M * 32 * sizeof(T);
