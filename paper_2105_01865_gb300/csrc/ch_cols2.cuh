@@ -1,0 +1,207 @@
+// Two-column form of the column line solver (y- and z-lines; Eqs.
+// eq-fac-2, eq-fac-3 of arXiv 2105.01865).  Lane l of a warp owns the two
+// adjacent lines at x = i0 + 2l, i0 + 2l + 1, so a tile covers 64 lines and
+// every row access is one 256-byte coalesced pair access; both lines advance
+// with one paired instruction (FFMA2 for FP32) per multiply-add, and each
+// broadcast coefficient load serves two lines.  Warp w owns rows
+// [w R, w R + R) in registers; the chunk end states are composed across warps
+// through shared memory with the host-precomputed 2x2 chunk transfer
+// matrices, as in ch_solve_cols.
+//
+// With UPDATE the solved increment is added to C (q^{l+1} = q^l + dq), C
+// having been prefetched into shared memory by cp.async at kernel entry when
+// it fits, so its latency hides behind the solve.  Requires even nx (pairs
+// are 8/16-byte aligned).
+#pragma once
+
+#include "ch_explicit2.cuh"
+
+namespace chg {
+
+// dynamic shared memory of ch_solve_cols2 (in bytes), by part
+template <typename T, int R, int NW, bool UPDATE>
+struct Cols2Smem {
+    static constexpr size_t kPair = 2 * sizeof(T);
+    static constexpr size_t kQueues = (size_t)NW * 2 * 32 * kPair * 2;  // forward + backward chunk states
+    static constexpr size_t kWacc = (size_t)NW * 4 * 32 * kPair;        // periodic only
+    static constexpr size_t kRows = (size_t)NW * R;
+    static constexpr bool kPrefetch = UPDATE && kRows * 32 * kPair <= 96 * 1024;
+    static constexpr size_t kCbuf = kPrefetch ? kRows * 32 * kPair : 0;
+    static constexpr size_t bytes(bool periodic) { return kQueues + (periodic ? kWacc : 0) + kCbuf; }
+    static constexpr size_t kMax = kQueues + kWacc + kCbuf;
+};
+
+__device__ __forceinline__ void cp_async_pair(Pr<float>* dst, const float* src) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_pair(Pr<double>* dst, const double* src) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src) : "memory");
+}
+
+// two duplicated pairs (a, a, b, b) from a coefficient table row
+template <typename T>
+__device__ __forceinline__ void ld_pairs(const T* p, Pr<T>& a, Pr<T>& b) {
+    const V4<T> c = ldv4(p);
+    a = mk(c.x, c.y);
+    b = mk(c.z, c.w);
+}
+
+// Up to 128 registers a thread: a lane holds R row pairs.
+template <typename T, int R, int NW, bool UPDATE>
+__global__ void __launch_bounds__(NW * 32, (512 / (NW * 32)) > 0 ? 512 / (NW * 32) : 1)
+ch_solve_cols2(T* __restrict__ a, T* __restrict__ Cf, int nx, int64_t outer_stride, int64_t line_stride,
+               CCoef<T> cf, unsigned int* status) {
+    using SM = Cols2Smem<T, R, NW, UPDATE>;
+    extern __shared__ __align__(16) unsigned char cols2_raw[];
+    Pr<T>* fq = reinterpret_cast<Pr<T>*>(cols2_raw);       // [NW][2][32]
+    Pr<T>* bq = fq + NW * 2 * 32;                          // [NW][2][32]
+    Pr<T>* wacc = bq + NW * 2 * 32;                        // [NW][4][32] (periodic)
+    Pr<T>* cbuf = wacc + (cf.periodic ? NW * 4 * 32 : 0);  // [rows][32] (prefetched C)
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int xblocks = (nx + 63) >> 6;
+    const int xb = blockIdx.x % xblocks;
+    const int64_t outer = blockIdx.x / xblocks;
+    const int ia = xb * 64 + 2 * lane;
+    const bool valid = ia < nx;  // nx even: ia + 1 < nx as well
+    const int n = cf.n;
+    const int j0 = w * R;
+    const bool per = cf.periodic;
+    const int64_t g = outer * outer_stride + ia + (int64_t)j0 * line_stride;
+
+    if (SM::kPrefetch) {
+#pragma unroll
+        for (int i = 0; i < R; ++i)
+            if (valid && j0 + i < n) cp_async_pair(&cbuf[(j0 + i) * 32 + lane], Cf + g + (int64_t)i * line_stride);
+        cp_async_commit();
+    }
+    Pr<T> v[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+        v[i] = (valid && j0 + i < n) ? ldp(a + g + (int64_t)i * line_stride) : sp<T>(T(0));
+
+    // forward elimination from a zero state over this warp's rows
+    Pr<T> y1 = sp<T>(T(0)), y2 = sp<T>(T(0));
+    Pr<T> acc0 = sp<T>(T(0)), acc1 = acc0, acc2 = acc0, acc3 = acc0;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        Pr<T> nl1, nl2;
+        ld_pairs(cf.fwdp + 4 * (j0 + i), nl1, nl2);
+        const Pr<T> y = fma2(nl1, y1, fma2(nl2, y2, v[i]));
+        y2 = y1;
+        y1 = y;
+        if (per) {
+            Pr<T> w0, w1, w2, w3;
+            ld_pairs(cf.Wp + 8 * (j0 + i), w0, w1);
+            ld_pairs(cf.Wp + 8 * (j0 + i) + 4, w2, w3);
+            acc0 = fma2(w0, v[i], acc0);
+            acc1 = fma2(w1, v[i], acc1);
+            acc2 = fma2(w2, v[i], acc2);
+            acc3 = fma2(w3, v[i], acc3);
+        }
+    }
+    fq[(w * 2 + 0) * 32 + lane] = y1;
+    fq[(w * 2 + 1) * 32 + lane] = y2;
+    if (per) {
+        wacc[(w * 4 + 0) * 32 + lane] = acc0;
+        wacc[(w * 4 + 1) * 32 + lane] = acc1;
+        wacc[(w * 4 + 2) * 32 + lane] = acc2;
+        wacc[(w * 4 + 3) * 32 + lane] = acc3;
+    }
+    __syncthreads();
+    // incoming state: compose the chunks of warps 0 .. w-1
+    Pr<T> s0 = sp<T>(T(0)), s1 = sp<T>(T(0));
+    for (int u = 0; u < w; ++u) {
+        const V4<T> Pm = ld4(cf.P + 4 * u);
+        const Pr<T> n0 = fma2(sp<T>(Pm.x), s0, fma2(sp<T>(Pm.y), s1, fq[(u * 2 + 0) * 32 + lane]));
+        const Pr<T> n1 = fma2(sp<T>(Pm.z), s0, fma2(sp<T>(Pm.w), s1, fq[(u * 2 + 1) * 32 + lane]));
+        s0 = n0;
+        s1 = n1;
+    }
+    Pr<T> sv0 = sp<T>(T(0)), sv1 = sv0, sv2 = sv0, sv3 = sv0;
+    if (per) {
+        Pr<T> t0 = sp<T>(T(0)), t1 = t0, t2 = t0, t3 = t0;
+#pragma unroll
+        for (int u = 0; u < NW; ++u) {
+            t0 = add(t0, wacc[(u * 4 + 0) * 32 + lane]);
+            t1 = add(t1, wacc[(u * 4 + 1) * 32 + lane]);
+            t2 = add(t2, wacc[(u * 4 + 2) * 32 + lane]);
+            t3 = add(t3, wacc[(u * 4 + 3) * 32 + lane]);
+        }
+        const V4<T> r0 = ld4(cf.S), r1 = ld4(cf.S + 4), r2 = ld4(cf.S + 8), r3 = ld4(cf.S + 12);
+        sv0 = fma2(sp<T>(r0.x), t0, fma2(sp<T>(r0.y), t1, fma2(sp<T>(r0.z), t2, mul(sp<T>(r0.w), t3))));
+        sv1 = fma2(sp<T>(r1.x), t0, fma2(sp<T>(r1.y), t1, fma2(sp<T>(r1.z), t2, mul(sp<T>(r1.w), t3))));
+        sv2 = fma2(sp<T>(r2.x), t0, fma2(sp<T>(r2.y), t1, fma2(sp<T>(r2.z), t2, mul(sp<T>(r2.w), t3))));
+        sv3 = fma2(sp<T>(r3.x), t0, fma2(sp<T>(r3.y), t1, fma2(sp<T>(r3.z), t2, mul(sp<T>(r3.w), t3))));
+    }
+    y1 = s0;
+    y2 = s1;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        Pr<T> nl1, nl2;
+        ld_pairs(cf.fwdp + 4 * (j0 + i), nl1, nl2);
+        const Pr<T> y = fma2(nl1, y1, fma2(nl2, y2, v[i]));
+        y2 = y1;
+        y1 = y;
+        T d0, d1;
+        ldv2(cf.dinvp + 2 * (j0 + i), d0, d1);
+        v[i] = mul(y, mk(d0, d1));
+    }
+    // back substitution from a zero state over this warp's rows
+    Pr<T> x1 = sp<T>(T(0)), x2 = sp<T>(T(0));
+#pragma unroll
+    for (int i = R - 1; i >= 0; --i) {
+        Pr<T> nu1, nu2;
+        ld_pairs(cf.bwdp + 4 * (j0 + i), nu1, nu2);
+        const Pr<T> x = fma2(nu1, x1, fma2(nu2, x2, v[i]));
+        x2 = x1;
+        x1 = x;
+    }
+    bq[(w * 2 + 0) * 32 + lane] = x1;
+    bq[(w * 2 + 1) * 32 + lane] = x2;
+    if (SM::kPrefetch) cp_async_wait<0>();
+    __syncthreads();
+    s0 = sp<T>(T(0));
+    s1 = sp<T>(T(0));
+    for (int u = NW - 1; u > w; --u) {
+        const V4<T> Qm = ld4(cf.Q + 4 * u);
+        const Pr<T> n0 = fma2(sp<T>(Qm.x), s0, fma2(sp<T>(Qm.y), s1, bq[(u * 2 + 0) * 32 + lane]));
+        const Pr<T> n1 = fma2(sp<T>(Qm.z), s0, fma2(sp<T>(Qm.w), s1, bq[(u * 2 + 1) * 32 + lane]));
+        s0 = n0;
+        s1 = n1;
+    }
+    x1 = s0;
+    x2 = s1;
+    bool bad = false;
+    T* dst = (UPDATE ? Cf : a) + g;
+#pragma unroll
+    for (int i = R - 1; i >= 0; --i) {
+        Pr<T> nu1, nu2;
+        ld_pairs(cf.bwdp + 4 * (j0 + i), nu1, nu2);
+        const Pr<T> x = fma2(nu1, x1, fma2(nu2, x2, v[i]));
+        x2 = x1;
+        x1 = x;
+        Pr<T> o = x;
+        if (per) {
+            Pr<T> z0, z1, z2, z3;
+            ld_pairs(cf.Zp + 8 * (j0 + i), z0, z1);
+            ld_pairs(cf.Zp + 8 * (j0 + i) + 4, z2, z3);
+            o = fma2(z0, sv0, fma2(z1, sv1, fma2(z2, sv2, fma2(z3, sv3, o))));
+        }
+        if (valid && j0 + i < n) {
+            T* pd = dst + (int64_t)i * line_stride;
+            if (UPDATE) {
+                const Pr<T> cold = SM::kPrefetch ? cbuf[(j0 + i) * 32 + lane] : ldp(pd);
+                const Pr<T> cnew = add(cold, o);
+                bad |= !isfinite(cnew.x()) || !isfinite(cnew.y());
+                stp(pd, cnew);
+            } else {
+                stp(pd, o);
+            }
+        }
+    }
+    if (UPDATE && bad) atomicOr(status, 1u);
+}
+
+}  // namespace chg

@@ -713,6 +713,12 @@ struct CCoef {
     const T* __restrict__ P;    // [NW][4]    forward chunk transfer matrices
     const T* __restrict__ Q;    // [NW][4]    backward chunk transfer matrices
     const T* __restrict__ S;    // [4][4]
+    // two-column form: duplicated pairs
+    const T* __restrict__ fwdp;   // [rows][4]: -l1, -l1, -l2, -l2
+    const T* __restrict__ dinvp;  // [rows][2]: 1/u0, 1/u0
+    const T* __restrict__ bwdp;   // [rows][4]: -u1/u0 (x2), -u2/u0 (x2)
+    const T* __restrict__ Wp;     // [rows][8]: W_m (x2), periodic only
+    const T* __restrict__ Zp;     // [rows][8]: -Z_m (x2), periodic only
     int n;
     int periodic;
 };

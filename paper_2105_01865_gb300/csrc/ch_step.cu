@@ -14,6 +14,7 @@
 #include "ch_internal.h"
 #include "ch_explicit2.cuh"
 #include "ch_kernels.cuh"
+#include "ch_cols2.cuh"
 #include "line_tables.h"
 
 using namespace chg;
@@ -166,6 +167,11 @@ CCoef<T> ccoef(const LineTables& lt) {
     k.P = b + L.P;
     k.Q = b + L.Q;
     k.S = b + L.S;
+    k.fwdp = b + L.fwdp;
+    k.dinvp = b + L.dinvp;
+    k.bwdp = b + L.bwdp;
+    k.Wp = b + L.Wp;
+    k.Zp = b + L.Zp;
     k.n = lt.n;
     k.periodic = lt.periodic;
     return k;
@@ -189,10 +195,59 @@ int launch_cols_rn(ch_handle* h, int l, int dir, T* r, T* Cupd) {
     return CH_OK;
 }
 
+// Two-column form (even nx): lanes own pairs of adjacent lines.
+template <typename T, int R, int NW>
+int launch_cols2_rn(ch_handle* h, int l, int dir, T* r, T* Cupd) {
+    const int nx = (int)h->n[0], ny = (int)h->n[1], nz = (int)h->n[2];
+    const CCoef<T> cf = ccoef<T>(h->lines[dir][l]);
+    const unsigned xblocks = (unsigned)((nx + 63) / 64);
+    const bool per = cf.periodic != 0;
+    if (dir == 1) {
+        ch_solve_cols2<T, R, NW, false><<<xblocks * (unsigned)nz, NW * 32,
+                                          Cols2Smem<T, R, NW, false>::bytes(per), h->stream>>>(
+            r, nullptr, nx, (int64_t)nx * ny, nx, cf, h->status);
+    } else if (Cupd) {
+        ch_solve_cols2<T, R, NW, true><<<xblocks * (unsigned)ny, NW * 32,
+                                         Cols2Smem<T, R, NW, true>::bytes(per), h->stream>>>(
+            r, Cupd, nx, nx, (int64_t)nx * ny, cf, h->status);
+    } else {
+        ch_solve_cols2<T, R, NW, false><<<xblocks * (unsigned)ny, NW * 32,
+                                          Cols2Smem<T, R, NW, false>::bytes(per), h->stream>>>(
+            r, nullptr, nx, nx, (int64_t)nx * ny, cf, h->status);
+    }
+    CHG_CUDA(h, cudaGetLastError());
+    return CH_OK;
+}
+
+template <typename T, int R, int NW>
+int set_attrs_cols2(ch_handle* h) {
+    CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_cols2<T, R, NW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)Cols2Smem<T, R, NW, false>::kMax));
+    CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_cols2<T, R, NW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)Cols2Smem<T, R, NW, true>::kMax));
+    return CH_OK;
+}
+
+template <typename T>
+int set_attrs_cols2_all(ch_handle* h) {
+    int rc = set_attrs_cols2<T, 1, 8>(h);
+    if (rc == CH_OK) rc = set_attrs_cols2<T, 2, 8>(h);
+    if (rc == CH_OK) rc = set_attrs_cols2<T, 4, 8>(h);
+    if (rc == CH_OK) rc = set_attrs_cols2<T, 8, 8>(h);
+    if (rc == CH_OK) rc = set_attrs_cols2<T, 16, 8>(h);
+    if (rc == CH_OK) rc = set_attrs_cols2<T, 16, 16>(h);
+    return rc;
+}
+
 // Which strided directions use the column solver (bit 1: y, bit 2: z); the
-// others use the shared-memory tile solver.  Default: z only (measured).
+// others use the shared-memory tile solver.  Default: both (measured with the
+// two-column form; the one-column form alone was slower than the tile for y).
 #ifndef CH_COLUMN_DIRS
-#define CH_COLUMN_DIRS 4
+#define CH_COLUMN_DIRS 6
+#endif
+// Use the two-column form of the column solver when nx is even.
+#ifndef CH_COLUMN_PAIRS
+#define CH_COLUMN_PAIRS 1
 #endif
 
 // Column solver for y/z lines (shape chosen by col_shape); -1 if none.
@@ -200,6 +255,23 @@ template <typename T>
 int launch_cols(ch_handle* h, int l, int dir, T* r, T* Cupd) {
     const LineTables& lt = h->lines[dir][l];
     if (!lt.col || !((CH_COLUMN_DIRS >> dir) & 1)) return -1;
+    // two-column form: FP32 only (an FP64 lane would hold 4 R registers of rows)
+    if constexpr (sizeof(T) == 4) {
+        if (CH_COLUMN_PAIRS && h->n[0] % 2 == 0) {
+            if (lt.nw == 8) {
+                switch (lt.R) {
+                    case 1: return launch_cols2_rn<T, 1, 8>(h, l, dir, r, Cupd);
+                    case 2: return launch_cols2_rn<T, 2, 8>(h, l, dir, r, Cupd);
+                    case 4: return launch_cols2_rn<T, 4, 8>(h, l, dir, r, Cupd);
+                    case 8: return launch_cols2_rn<T, 8, 8>(h, l, dir, r, Cupd);
+                    case 16: return launch_cols2_rn<T, 16, 8>(h, l, dir, r, Cupd);
+                    default: return -1;
+                }
+            }
+            if (lt.nw == 16 && lt.R == 16) return launch_cols2_rn<T, 16, 16>(h, l, dir, r, Cupd);
+            // 32 warps leave 64 registers a thread: the one-column form below
+        }
+    }
     if (lt.nw == 8) {
         switch (lt.R) {
             case 1: return launch_cols_rn<T, 1, 8>(h, l, dir, r, Cupd);
@@ -317,6 +389,8 @@ int set_smem_attrs(ch_handle* h) {
     if (rc == CH_OK) rc = set_attrs_m<T, 8>(h);
     if (rc == CH_OK) rc = set_attrs_m<T, 16>(h);
     if (rc == CH_OK) rc = set_attrs_m<T, 32>(h);
+    if constexpr (sizeof(T) == 4)
+        if (rc == CH_OK) rc = set_attrs_cols2_all<T>(h);
     return rc;
 }
 

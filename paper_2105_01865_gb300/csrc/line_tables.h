@@ -287,7 +287,9 @@ namespace chg {
 // rows (zero padding past n), then per warp-chunk the forward transfer matrix
 // P_w = A_{b-1} ... A_a and the backward one Q_w = B_a ... B_{b-1}.
 struct ColLayout {
-    size_t fwd, bwd, W, Z, P, Q, S, total;
+    size_t fwd, bwd, W, Z, P, Q, S;
+    size_t fwdp, dinvp, bwdp, Wp, Zp;  // the same rows as duplicated pairs (two-column form)
+    size_t total;
 };
 
 inline ColLayout col_layout(int nw, int R) {
@@ -301,6 +303,11 @@ inline ColLayout col_layout(int nw, int R) {
     L.P = off;   off += (size_t)nw * 4;
     L.Q = off;   off += (size_t)nw * 4;
     L.S = off;   off += 16;
+    L.fwdp = off;  off += rows * 4;
+    L.dinvp = off; off += rows * 2;
+    L.bwdp = off;  off += rows * 4;
+    L.Wp = off;    off += rows * 8;
+    L.Zp = off;    off += rows * 8;
     L.total = (off + 63) / 64 * 64;
     return L;
 }
@@ -315,10 +322,22 @@ inline std::vector<double> col_tables(const LineFactors& F, int nw, int R) {
         t[L.fwd + 4 * (size_t)j + 2] = F.dinv[j];
         t[L.bwd + 2 * (size_t)j + 0] = F.u1s[j];
         t[L.bwd + 2 * (size_t)j + 1] = F.u2s[j];
+        // two-column form: negated multipliers duplicated for paired FMAs
+        for (int e = 0; e < 2; ++e) {
+            t[L.fwdp + 4 * (size_t)j + e] = -F.l1[j];
+            t[L.fwdp + 4 * (size_t)j + 2 + e] = -F.l2[j];
+            t[L.dinvp + 2 * (size_t)j + e] = F.dinv[j];
+            t[L.bwdp + 4 * (size_t)j + e] = -F.u1s[j];
+            t[L.bwdp + 4 * (size_t)j + 2 + e] = -F.u2s[j];
+        }
         if (F.periodic)
             for (int m = 0; m < 4; ++m) {
                 t[L.W + 4 * (size_t)j + m] = F.W[(size_t)j * 4 + m];
                 t[L.Z + 4 * (size_t)j + m] = F.Z[(size_t)j * 4 + m];
+                for (int e = 0; e < 2; ++e) {
+                    t[L.Wp + 8 * (size_t)j + 2 * m + e] = F.W[(size_t)j * 4 + m];
+                    t[L.Zp + 8 * (size_t)j + 2 * m + e] = -F.Z[(size_t)j * 4 + m];
+                }
             }
     }
     for (int w = 0; w < nw; ++w) {
