@@ -296,6 +296,65 @@ def multires_leg(args, dev, flush):
     return out
 
 
+def scheme_leg(args, dev, W):
+    """Time to solution of the paper's split scheme against the standard
+    explicit 25-point scheme (Eq. eq-disbi) it replaces (Sec. 4.1 reports
+    dt = 2e-3 against 5e-5 for its shear drop): both FP32, on the bench's
+    shear-drop box, from the same C0 to the same time T = 10 steps of the
+    split scheme, each at its largest stable dt (linear bound x 0.9, CFL
+    0.5 h / max|u|).  Per-kernel times of the standard scheme come from
+    ch_profile_step (chemical potential, advection, update)."""
+    import math
+
+    import torch
+    from paper_2105_01865_gb300 import capi, inputs, stability
+    from paper_2105_01865_gb300.solver import Solver
+    f = inputs.shear_drop_box(W["nx"], W["ny"], W["nz"])
+    h, bc, cn, pe = f["h"], f["bc"], f["cn"], f["pe"]
+    ncell = W["nx"] * W["ny"] * W["nz"]
+    cfl = 0.5 * h / 0.5
+    dt_split = min(0.9 * stability.stable_dt(f["shape"], h, bc, cn, pe), cfl)
+    dt_std_max = min(0.9 * stability.stable_dt_standard(f["shape"], h, bc, cn, pe), cfl)
+    n_split = 10
+    T = n_split * dt_split
+    n_std = int(math.ceil(T / dt_std_max))
+    dt_std = T / n_std
+    C0 = torch.as_tensor(f["C"], dtype=torch.float32)
+    out = {}
+    fields = {}
+    for name, scheme, dt, n in (("split", "split", dt_split, n_split), ("standard", "standard", dt_std, n_std)):
+        s = Solver(f["shape"], h, bc, cn, pe, dt, f["C"], precision="f32", advect=True, device=dev, scheme=scheme)
+        s.set_velocity_fine(*f["vel"])
+        s.step(1)                     # captures the step graph
+        s.C.copy_(C0.to(dev))         # restart from C0
+        s._order()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(s.stream):
+            a.record(s.stream)
+            s.step(n)
+            b.record(s.stream)
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b)
+        fields[name] = s.field()
+        out[name] = dict(dt=dt, steps=n, ms=ms, ms_per_step=ms / n)
+        if name == "standard":
+            kms = [0.0] * 4
+            for _ in range(3):
+                kms = [x + y for x, y in zip(kms, capi.ch_profile_step(s.handle, 1))]
+            names = ("ch_std_mu", "advection", "ch_std_update")
+            kbytes = (8.0, 80.0 / 3.0 - 8.0, 24.0)  # algorithmic B/cell: mu, advection (C, u, v, w; H), update
+            out[name]["kernels"] = {nm: dict(ms=k / 3, gbs=b * ncell / (k / 3 * 1e-3) / 1e9)
+                                    for nm, k, b in zip(names, kms[:3], kbytes)}
+        s.close()
+    ref = fields["split"]
+    out.update(T=T, dt_ratio=dt_split / dt_std_max,
+               time_to_solution_speedup=out["standard"]["ms"] / out["split"]["ms"],
+               rel_l2_standard_vs_split=float(np.linalg.norm(fields["standard"] - ref) / np.linalg.norm(ref)),
+               paper_dt_ratio=2e-3 / 5e-5)
+    return out
+
+
 def gpu_arm(args):
     import torch
     import torch.distributed as dist
@@ -416,6 +475,7 @@ def gpu_arm(args):
 
     batched = batched_leg(args, dev, flush, rank, world)
     multires = multires_leg(args, dev, flush) if not args.no_multires else None
+    schemes = scheme_leg(args, dev, W) if not args.no_scheme else None
     clk.__exit__(None, None, None)
     clocks = clk.summary()
 
@@ -432,7 +492,8 @@ def gpu_arm(args):
                 config=dict(workload=W["name"], global_batch=world, seq_len=0,
                             parallelism=f"replicas{world}", cells=ncell, precision="f32 fields, f64 reductions",
                             l2="flushed between timed steps (256 MB write); working set 235 MB > L2"),
-                roofline=roofline, e2e=e2e, fp64_plain=fp64, batched=batched, multires=multires, clocks=clocks,
+                roofline=roofline, e2e=e2e, fp64_plain=fp64, batched=batched, multires=multires,
+                scheme_comparison=schemes, clocks=clocks,
                 gpu_launches=args.steps * s32.launches_per_step())
     if rank == 0 and not args.no_cpu_baseline:
         cells, times = run_oracle(1, 0)
@@ -457,6 +518,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-multires", action="store_true", help="skip the 1024x1024x512 transfer + step leg")
+    ap.add_argument("--no-scheme", action="store_true", help="skip the split vs standard scheme comparison")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -61,6 +61,10 @@ extern "C" {
 #define CH_F32 0         /* float fields, float arithmetic; FP64 reductions */
 #define CH_F64 1         /* double everywhere (the plain method) */
 
+/* time-stepping scheme (ch_params.scheme) */
+#define CH_SCHEME_SPLIT 0
+#define CH_SCHEME_STANDARD 1
+
 typedef struct ch_params {
     int64_t nx, ny, nz;   /* fine cells per direction, each >= 5 */
     double h;             /* uniform fine spacing (Sec. 3: same h in all directions) */
@@ -72,7 +76,10 @@ typedef struct ch_params {
     double w;             /* biharmonic weight: A_d = (w Cn^2/h^4)[1,-4,6,-4,1]; 4 = Eq. eq-a3d as printed */
     double weno_eps;      /* WENO5 regulariser (1e-6) */
     int32_t advect;       /* 0: u = 0, no advection term; 1: advect with the fine face velocity */
-    int32_t reserved;     /* must be 0 */
+    int32_t scheme;       /* CH_SCHEME_SPLIT (0): the paper's A_x + A_y + A_z Crank-Nicolson step,
+                             approximately factorised (Sec. 3.1); CH_SCHEME_STANDARD (1): the standard
+                             25-point biharmonic of Eq. eq-disbi (lap_h applied twice), all terms
+                             explicit in the same RK3 -- the comparison scheme of Sec. 4.1 */
     /* optional coarse (Navier-Stokes) mesh for the velocity transfer; all 0/NULL if unused.
      * Host arrays of face coordinates, read during ch_create only: xf has ncx+1 entries,
      * starting at 0 and ending at nx*h (likewise y, z).  Any (stretched) spacing;

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_PKG, "libch.so")
 CH_OK, CH_EINVAL, CH_ECUDA, CH_ENONFINITE, CH_ETIMEOUT, CH_ENOMEM = range(6)
 CH_PERIODIC, CH_NOFLUX = 0, 1
 CH_F32, CH_F64 = 0, 1
+CH_SCHEME_SPLIT, CH_SCHEME_STANDARD = 0, 1
 
 
 class CHError(RuntimeError):
@@ -35,7 +36,7 @@ class ch_params(ctypes.Structure):
         ("precision", ctypes.c_int32),
         ("cn", ctypes.c_double), ("pe", ctypes.c_double), ("dt", ctypes.c_double),
         ("w", ctypes.c_double), ("weno_eps", ctypes.c_double),
-        ("advect", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("advect", ctypes.c_int32), ("scheme", ctypes.c_int32),
         ("ncx", ctypes.c_int64), ("ncy", ctypes.c_int64), ("ncz", ctypes.c_int64),
         ("xf_coarse", ctypes.POINTER(ctypes.c_double)),
         ("yf_coarse", ctypes.POINTER(ctypes.c_double)),
@@ -112,8 +113,10 @@ def _ptr(t):
     return ctypes.c_void_p(0 if t is None else t.data_ptr())
 
 
-def make_params(shape, h, bc, cn, pe, dt, precision=CH_F32, w=4.0, weno_eps=1e-6, advect=False, coarse_faces=None):
-    """Fill a ch_params.  shape = (nz, ny, nx); coarse_faces = (xf, yf, zf) numpy arrays or None.
+def make_params(shape, h, bc, cn, pe, dt, precision=CH_F32, w=4.0, weno_eps=1e-6, advect=False, coarse_faces=None,
+                scheme=0):
+    """Fill a ch_params.  shape = (nz, ny, nx); coarse_faces = (xf, yf, zf) numpy arrays or None;
+    scheme = CH_SCHEME_SPLIT (0) or CH_SCHEME_STANDARD (1).
     The returned object keeps the coarse arrays alive as attribute ``_keep``."""
     nz, ny, nx = shape
     p = ch_params()
@@ -123,7 +126,7 @@ def make_params(shape, h, bc, cn, pe, dt, precision=CH_F32, w=4.0, weno_eps=1e-6
     p.precision = precision
     p.cn, p.pe, p.dt, p.w, p.weno_eps = cn, pe, dt, w, weno_eps
     p.advect = 1 if advect else 0
-    p.reserved = 0
+    p.scheme = scheme
     keep = []
     if coarse_faces is not None:
         arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in coarse_faces]

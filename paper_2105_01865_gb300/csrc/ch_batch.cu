@@ -199,7 +199,7 @@ bool batch_params_ok(const ch_params* b, int nbox) {
     if (!b || nbox < 1 || nbox > 65535) return false;
     for (int i = 0; i < nbox; ++i) {
         const ch_params& p = b[i];
-        if (p.precision != CH_F32 || p.advect != 0 || p.reserved != 0) return false;
+        if (p.precision != CH_F32 || p.advect != 0 || p.scheme != CH_SCHEME_SPLIT) return false;
         if (p.ncx || p.ncy || p.ncz || p.xf_coarse || p.yf_coarse || p.zf_coarse) return false;
         if (p.nx < 6 || p.ny < 5 || p.nz < 5 || (p.nx & 1)) return false;
         if (p.nx > 256 || p.ny > 256 || p.nz > 256) return false;

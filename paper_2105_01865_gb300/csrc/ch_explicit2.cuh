@@ -290,7 +290,7 @@ __device__ __forceinline__ void explicit_tile2(const T* C, const T* u, const T* 
             Pr<T> rhs = fma2(sp<T>(-a.impl), astar, mul(sp<T>(a.dtg), H));
             if (a.has_prev) rhs = fma2(sp<T>(a.dtr), hp, rhs);
             stp(Hout + idx, H);
-            stp(r + idx, rhs);
+            if (r) stp(r + idx, rhs);
         }
 #pragma unroll
         for (int m = 0; m < 5; ++m) q[m] = q[m + 1];

@@ -92,6 +92,10 @@ inline int fail(ch_handle* h, int code, const char* fmt, ...) {
 int launch_explicit_any(ch_handle* h, int l, const void* C, const void* Hprev, void* Hout, void* r);
 int launch_solve_any(ch_handle* h, int l, int dir, void* a, void* Cupd);
 int launch_step_any(ch_handle* h, void* C);  // one full step of the field C (direct launches)
+// -div(uC) alone into Hout (the standard scheme's advection; ch_step.cu)
+int launch_advection_any(ch_handle* h, const void* C, void* Hout);
+// one substep of the standard explicit scheme (ch_standard.cu); ev: 5 events or NULL
+int launch_substep_standard(ch_handle* h, int l, cudaEvent_t* ev);
 
 // multi-resolution entry points implemented in ch_mr.cu
 int mr_build_tables(ch_handle* h, const double* xf, const double* yf, const double* zf);

@@ -286,7 +286,7 @@ ch_explicit_rhs(const T* __restrict__ C, const T* __restrict__ u, const T* __res
             T rhs = a.dtg * H - a.impl * astar;
             if (a.has_prev) rhs += a.dtr * Hprev[idx];
             Hout[idx] = H;
-            r[idx] = rhs;
+            if (r) r[idx] = rhs;
         }
         // advance the z queue
 #pragma unroll

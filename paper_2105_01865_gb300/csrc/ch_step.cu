@@ -43,7 +43,8 @@ bool params_valid(const ch_params* p, char* why, size_t wl) {
         if (p->bc[d] != CH_PERIODIC && p->bc[d] != CH_NOFLUX) return bad("bc must be CH_PERIODIC or CH_NOFLUX");
     if (p->precision != CH_F32 && p->precision != CH_F64) return bad("precision must be CH_F32 or CH_F64");
     if (p->advect != 0 && p->advect != 1) return bad("advect must be 0 or 1");
-    if (p->reserved != 0) return bad("reserved must be 0");
+    if (p->scheme != CH_SCHEME_SPLIT && p->scheme != CH_SCHEME_STANDARD)
+        return bad("scheme must be CH_SCHEME_SPLIT or CH_SCHEME_STANDARD");
     const bool any_c = p->ncx || p->ncy || p->ncz || p->xf_coarse || p->yf_coarse || p->zf_coarse;
     if (any_c) {
         if (p->ncx < 4 || p->ncy < 4 || p->ncz < 4) return bad("coarse mesh needs >= 4 cells per direction");
@@ -317,8 +318,11 @@ int set_attrs_m(ch_handle* h) {
 }
 
 // Explicit RHS of substep l from C (and Hprev) into Hout and r.
+// With adv_only (the standard scheme's advection): Hout = -div(uC) only, no
+// diffusive or implicit term, no right-hand side written.
 template <typename T>
-int launch_explicit(ch_handle* h, int l, const T* C, const T* Hprev, T* Hout, T* r, cudaEvent_t* ev) {
+int launch_explicit(ch_handle* h, int l, const T* C, const T* Hprev, T* Hout, T* r, cudaEvent_t* ev,
+                    bool adv_only = false) {
     const ch_params& p = h->p;
     const int nx = (int)h->n[0], ny = (int)h->n[1], nz = (int)h->n[2];
     RhsArgs<T> a;
@@ -342,6 +346,14 @@ int launch_explicit(ch_handle* h, int l, const T* C, const T* Hprev, T* Hout, T*
     a.impl = (T)(alpha * p.dt * mob * kappa);
     a.eps = (T)p.weno_eps;
     a.has_prev = kRho[l] != 0.0;
+    if (adv_only) {
+        a.mob = T(0);
+        a.impl = T(0);
+        a.dtg = T(1);
+        a.dtr = T(0);
+        a.has_prev = 0;
+        r = nullptr;
+    }
     const T* u = p.advect ? (const T*)h->vel[0] : nullptr;
     const T* v = p.advect ? (const T*)h->vel[1] : nullptr;
     const T* w = p.advect ? (const T*)h->vel[2] : nullptr;
@@ -368,6 +380,7 @@ int launch_explicit(ch_handle* h, int l, const T* C, const T* Hprev, T* Hout, T*
 
 template <typename T>
 int launch_substep(ch_handle* h, int l, cudaEvent_t* ev = nullptr) {
+    if (h->p.scheme == CH_SCHEME_STANDARD) return launch_substep_standard(h, l, ev);
     T* C = (T*)h->C;
     T* r = (T*)h->r;
     int rc = launch_explicit<T>(h, l, C, (const T*)h->H[(l + 1) & 1], (T*)h->H[l & 1], r, ev);
@@ -402,6 +415,12 @@ int launch_explicit_any(ch_handle* h, int l, const void* C, const void* Hprev, v
     if (h->prec == CH_F64)
         return launch_explicit<double>(h, l, (const double*)C, (const double*)Hprev, (double*)Hout, (double*)r, nullptr);
     return launch_explicit<float>(h, l, (const float*)C, (const float*)Hprev, (float*)Hout, (float*)r, nullptr);
+}
+
+int launch_advection_any(ch_handle* h, const void* C, void* Hout) {
+    if (h->prec == CH_F64)
+        return launch_explicit<double>(h, 0, (const double*)C, nullptr, (double*)Hout, nullptr, nullptr, true);
+    return launch_explicit<float>(h, 0, (const float*)C, nullptr, (float*)Hout, nullptr, nullptr, true);
 }
 
 int launch_solve_any(ch_handle* h, int l, int dir, void* a, void* Cupd) {
@@ -496,7 +515,7 @@ int ch_create(const ch_params* p, void* C, void* work, size_t work_bytes, void* 
             h->nc[d] = nc[d];
             h->ncf[d] = nc[d] + (p->bc[d] == CH_NOFLUX ? 1 : 0);
         }
-    h->launches_per_step = 4 * kRK;
+    h->launches_per_step = p->scheme == CH_SCHEME_STANDARD ? (p->advect ? 3 : 2) * kRK : 4 * kRK;
 
     int rc = CH_OK;
     // warp-scan line-solve tables for every direction and substep

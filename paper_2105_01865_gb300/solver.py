@@ -17,11 +17,13 @@ class Solver:
     shape = (nz, ny, nx); bc = (bc_x, bc_y, bc_z) with capi.CH_PERIODIC /
     capi.CH_NOFLUX; precision "f32" or "f64".  C0 is a numpy or torch array of
     the initial volume fraction.  coarse_faces = (xf, yf, zf) enables the
-    velocity transfer from a stretched coarse mesh.
+    velocity transfer from a stretched coarse mesh.  scheme "split" is the
+    paper's factorised implicit biharmonic; "standard" the explicit 25-point
+    comparison scheme (Eq. eq-disbi).
     """
 
     def __init__(self, shape, h, bc, cn, pe, dt, C0, precision="f32", w=4.0, weno_eps=1e-6,
-                 advect=False, coarse_faces=None, device="cuda:0", stream=None):
+                 advect=False, coarse_faces=None, device="cuda:0", stream=None, scheme="split"):
         self.shape = tuple(int(s) for s in shape)
         self.bc = tuple(bc)
         self.dtype = torch.float64 if precision == "f64" else torch.float32
@@ -29,8 +31,11 @@ class Solver:
         # a dedicated stream by default, so ch_step runs as a captured CUDA graph
         self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
         prec = capi.CH_F64 if precision == "f64" else capi.CH_F32
+        if scheme not in ("split", "standard"):
+            raise ValueError("scheme must be 'split' or 'standard'")
         self.params = capi.make_params(self.shape, h, bc, cn, pe, dt, prec, w, weno_eps,
-                                       advect or coarse_faces is not None, coarse_faces)
+                                       advect or coarse_faces is not None, coarse_faces,
+                                       capi.CH_SCHEME_STANDARD if scheme == "standard" else capi.CH_SCHEME_SPLIT)
         nbytes = capi.ch_workspace_bytes(self.params)
         if nbytes == 0:
             raise capi.CHError(capi.CH_EINVAL, "invalid parameters")
