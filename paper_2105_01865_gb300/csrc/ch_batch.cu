@@ -4,7 +4,8 @@
 //
 // One RK3 step of every box is 12 phases (3 substeps x [explicit RHS, x-,
 // y-, z-line solve]).  Each phase is a flat list of work items over all
-// boxes (explicit tiles, groups of 8 x-lines, y/z column tiles).  Two
+// boxes (explicit tiles, groups of 16 x-lines, y/z tiles of 64 two-column
+// lines or 32-column shared-memory tiles).  Two
 // schedules run the same item functions:
 //  - persistent: one cooperative launch per step; CTAs walk the item list of
 //    a phase, then meet at a grid barrier whose spin is bounded in time (on
@@ -25,6 +26,7 @@
 #include "ch_internal.h"
 #include "ch_explicit2.cuh"
 #include "ch_kernels.cuh"
+#include "ch_cols2.cuh"
 #include "line_tables.h"
 
 using namespace chg;
@@ -44,6 +46,10 @@ struct BoxDesc {
     int M[3];
     RhsArgs<float> rhs[kRK];
     WCoef<float> lines[3][kRK];
+    // y and z: rows per warp of the two-column solver (8 warps of R rows),
+    // 0 where the line is too long and the shared-memory tile solver runs
+    int colR[2];
+    CCoef<float> cols[2][kRK];
 };
 
 struct BatchArgs {
@@ -95,11 +101,35 @@ __device__ bool grid_barrier(const BatchArgs& A) {
     return ok != 0;
 }
 
+// 16 x-lines: two per warp
 template <int M>
 __device__ __forceinline__ void x_item(const BoxDesc& B, int line0, int l) {
     const int warp = threadIdx.x >> 5;
-    const int64_t line = (int64_t)line0 + warp;
-    if (line < B.nlines_x) solve_x_line<float, M>(B.r, line, B.nx, B.lines[0][l]);
+    const int64_t line = (int64_t)line0 + 2 * warp;
+    if (line < B.nlines_x) solve_x_lines<float, M, 2>(B.r, line, B.nlines_x, B.nx, B.lines[0][l]);
+}
+
+// one 64-line tile of the two-column solver (y: UPDATE false, z: true)
+template <int R, bool UPDATE>
+__device__ __forceinline__ void cols_item(const BoxDesc& B, int tile, int l, unsigned char* smem, unsigned* status) {
+    if (!UPDATE)
+        solve_cols2_tile<float, R, kBWarps, false>(B.r, nullptr, B.nx, (int64_t)B.nx * B.ny, B.nx, B.cols[0][l],
+                                                   status, tile, smem);
+    else
+        solve_cols2_tile<float, R, kBWarps, true>(B.r, B.C, B.nx, B.nx, (int64_t)B.nx * B.ny, B.cols[1][l], status,
+                                                  tile, smem);
+}
+
+template <bool UPDATE>
+__device__ __forceinline__ void cols_dispatch(const BoxDesc& B, int R, int tile, int l, unsigned char* smem,
+                                              unsigned* status) {
+    switch (R) {
+        case 1: cols_item<1, UPDATE>(B, tile, l, smem, status); break;
+        case 2: cols_item<2, UPDATE>(B, tile, l, smem, status); break;
+        case 4: cols_item<4, UPDATE>(B, tile, l, smem, status); break;
+        case 8: cols_item<8, UPDATE>(B, tile, l, smem, status); break;
+        default: cols_item<16, UPDATE>(B, tile, l, smem, status); break;
+    }
 }
 
 template <int M, bool UPDATE>
@@ -131,6 +161,11 @@ __device__ void run_phase(const BatchArgs& A, int ph, int l, float* smem) {
                 case 4: x_item<4>(B, w.y, l); break;
                 default: x_item<MAXM>(B, w.y, l); break;
             }
+        } else if (w.z) {
+            if (ph == 2)
+                cols_dispatch<false>(B, B.colR[0], w.y, l, reinterpret_cast<unsigned char*>(smem), A.status);
+            else
+                cols_dispatch<true>(B, B.colR[1], w.y, l, reinterpret_cast<unsigned char*>(smem), A.status);
         } else {
             const int m = B.M[ph - 1];
             if (ph == 2) {
@@ -169,7 +204,7 @@ __global__ void __launch_bounds__(kBThreads, 3) ch_batch_persistent(BatchArgs A)
 // phase gets its own register allocation (the persistent kernel must carry
 // the largest of all phases).
 template <int PH, int MAXM>
-__global__ void __launch_bounds__(kBThreads) ch_batch_phase(BatchArgs A, int l) {
+__global__ void __launch_bounds__(kBThreads, PH == 0 ? 3 : 2) ch_batch_phase(BatchArgs A, int l) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     run_phase<MAXM>(A, PH, l, reinterpret_cast<float*>(smem_raw));
 }
@@ -194,6 +229,16 @@ __global__ void __launch_bounds__(kRedThreads) batch_mass_finish(const double* p
 }
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// shared memory of the two-column tiles for rows-per-warp up to maxR
+size_t cols2_smem_max(int maxR) {
+    size_t m = Cols2Smem<float, 1, kBWarps, true>::kMax;
+    if (maxR >= 2) m = std::max(m, Cols2Smem<float, 2, kBWarps, true>::kMax);
+    if (maxR >= 4) m = std::max(m, Cols2Smem<float, 4, kBWarps, true>::kMax);
+    if (maxR >= 8) m = std::max(m, Cols2Smem<float, 8, kBWarps, true>::kMax);
+    if (maxR >= 16) m = std::max(m, Cols2Smem<float, 16, kBWarps, true>::kMax);
+    return m;
+}
 
 bool batch_params_ok(const ch_params* b, int nbox) {
     if (!b || nbox < 1 || nbox > 65535) return false;
@@ -278,11 +323,19 @@ int build_items(ch_batch* b) {
                     lists[0].push_back({cost, make_int4(i, bx, by, bz)});
                 }
         const int nlx = ny * nz;
-        for (int l0 = 0; l0 < nlx; l0 += kBWarps)
-            lists[1].push_back({(double)std::min(kBWarps, nlx - l0) * nx, make_int4(i, l0, 0, 0)});
-        const int xb = (nx + 31) / 32;
-        for (int t = 0; t < xb * nz; ++t) lists[2].push_back({32.0 * warp_chunk(ny) * 32, make_int4(i, t, 0, 0)});
-        for (int t = 0; t < xb * ny; ++t) lists[3].push_back({32.0 * warp_chunk(nz) * 32, make_int4(i, t, 0, 0)});
+        for (int l0 = 0; l0 < nlx; l0 += 2 * kBWarps)
+            lists[1].push_back({(double)std::min(2 * kBWarps, nlx - l0) * nx, make_int4(i, l0, 0, 0)});
+        // y, z: 64-line two-column tiles (w = 1) or 32-column shared-memory tiles (w = 0)
+        const BoxDesc& B = b->boxes[i];
+        const int xb = (nx + 31) / 32, xb2 = (nx + 63) / 64;
+        if (B.colR[0])
+            for (int t = 0; t < xb2 * nz; ++t) lists[2].push_back({64.0 * ny, make_int4(i, t, 1, 0)});
+        else
+            for (int t = 0; t < xb * nz; ++t) lists[2].push_back({32.0 * warp_chunk(ny) * 32, make_int4(i, t, 0, 0)});
+        if (B.colR[1])
+            for (int t = 0; t < xb2 * ny; ++t) lists[3].push_back({64.0 * nz, make_int4(i, t, 1, 0)});
+        else
+            for (int t = 0; t < xb * ny; ++t) lists[3].push_back({32.0 * warp_chunk(nz) * 32, make_int4(i, t, 0, 0)});
     }
     for (int ph = 0; ph < 4; ++ph) {
         if (b->lpt)
@@ -414,7 +467,7 @@ int ch_batch_create(const ch_params* boxes, int nbox, void* const* C, void* work
     std::vector<std::vector<double>> tabs;
     size_t coef_total = 0;
     b->boxes.resize(nbox);
-    int maxM = 1;
+    int maxM = 1, maxR = 0;
     for (int i = 0; i < nbox; ++i) {
         const ch_params& p = b->params[i];
         BoxDesc& B = b->boxes[i];
@@ -452,6 +505,8 @@ int ch_batch_create(const ch_params* boxes, int nbox, void* const* C, void* work
         for (int d = 0; d < 3; ++d) {
             B.M[d] = warp_chunk((int)n[d]);
             maxM = std::max(maxM, B.M[d]);
+            int nw = 0, R = 0;
+            if (d > 0) B.colR[d - 1] = (col_shape((int)n[d], &nw, &R) && nw == kBWarps) ? R : 0;
             for (int l = 0; l < kRK; ++l) {
                 const double ck = (kGamma[l] + kRho[l]) * p.dt * mob / 2.0 * kappa;
                 const LineFactors F = line_factors((int)n[d], p.bc[d], ck);
@@ -461,10 +516,17 @@ int ch_batch_create(const ch_params* boxes, int nbox, void* const* C, void* work
                 }
                 tabs.push_back(warp_tables(F, B.M[d]));
                 coef_total += align256(tabs.back().size() * sizeof(float));
+                if (d > 0 && B.colR[d - 1]) {
+                    tabs.push_back(col_tables(F, kBWarps, B.colR[d - 1]));
+                    coef_total += align256(tabs.back().size() * sizeof(float));
+                }
             }
+            if (d > 0 && B.colR[d - 1]) maxR = std::max(maxR, B.colR[d - 1]);
         }
     }
+    // dynamic shared memory: the larger of the y/z tile and the two-column buffers
     b->smem = (size_t)32 * maxM * 32 * sizeof(float);
+    if (maxR) b->smem = std::max(b->smem, cols2_smem_max(maxR));
     b->max_m = maxM;
     int rc = CH_OK;
     if (cudaMalloc(&b->coef_buf, coef_total) != cudaSuccess) rc = CH_ENOMEM;
@@ -474,22 +536,48 @@ int ch_batch_create(const ch_params* boxes, int nbox, void* const* C, void* work
         int q = 0;
         for (int i = 0; i < nbox; ++i)
             for (int d = 0; d < 3; ++d)
-                for (int l = 0; l < kRK; ++l, ++q) {
-                    const std::vector<double>& t = tabs[q];
-                    for (size_t e = 0; e < t.size(); ++e) host[off / sizeof(float) + e] = (float)t[e];
-                    const float* base = (const float*)((char*)b->coef_buf + off);
-                    const WarpLayout L = warp_layout(b->boxes[i].M[d]);
-                    WCoef<float>& w = b->boxes[i].lines[d][l];
-                    w.fwd = base + L.fwd;
-                    w.bwd = base + L.bwd;
-                    w.W = base + L.W;
-                    w.Z = base + L.Z;
-                    w.Pf = base + L.Pf;
-                    w.Pb = base + L.Pb;
-                    w.S = base + L.S;
-                    w.n = (int)(d == 0 ? b->params[i].nx : d == 1 ? b->params[i].ny : b->params[i].nz);
-                    w.periodic = b->params[i].bc[d] == CH_PERIODIC;
-                    off += align256(t.size() * sizeof(float));
+                for (int l = 0; l < kRK; ++l) {
+                    const int nd = (int)(d == 0 ? b->params[i].nx : d == 1 ? b->params[i].ny : b->params[i].nz);
+                    const int per = b->params[i].bc[d] == CH_PERIODIC;
+                    {
+                        const std::vector<double>& t = tabs[q++];
+                        for (size_t e = 0; e < t.size(); ++e) host[off / sizeof(float) + e] = (float)t[e];
+                        const float* base = (const float*)((char*)b->coef_buf + off);
+                        const WarpLayout L = warp_layout(b->boxes[i].M[d]);
+                        WCoef<float>& w = b->boxes[i].lines[d][l];
+                        w.fwd = base + L.fwd;
+                        w.bwd = base + L.bwd;
+                        w.W = base + L.W;
+                        w.Z = base + L.Z;
+                        w.Pf = base + L.Pf;
+                        w.Pb = base + L.Pb;
+                        w.S = base + L.S;
+                        w.n = nd;
+                        w.periodic = per;
+                        off += align256(t.size() * sizeof(float));
+                    }
+                    if (d > 0 && b->boxes[i].colR[d - 1]) {
+                        const std::vector<double>& t = tabs[q++];
+                        for (size_t e = 0; e < t.size(); ++e) host[off / sizeof(float) + e] = (float)t[e];
+                        const float* base = (const float*)((char*)b->coef_buf + off);
+                        const ColLayout L = col_layout(kBWarps, b->boxes[i].colR[d - 1]);
+                        CCoef<float>& c = b->boxes[i].cols[d - 1][l];
+                        c.fwd = base + L.fwd;
+                        c.bwd = base + L.bwd;
+                        c.W = base + L.W;
+                        c.Z = base + L.Z;
+                        c.P = base + L.P;
+                        c.Q = base + L.Q;
+                        c.S = base + L.S;
+                        c.fwdp = base + L.fwdp;
+                        c.dinvp = base + L.dinvp;
+                        c.bwdp = base + L.bwdp;
+                        c.Wp = base + L.Wp;
+                        c.Zp = base + L.Zp;
+                        c.n = nd;
+                        c.periodic = per;
+                        off += align256(t.size() * sizeof(float));
+                    }
                 }
         if (cudaMemcpy(b->coef_buf, host.data(), coef_total, cudaMemcpyHostToDevice) != cudaSuccess) rc = CH_ECUDA;
     }

@@ -48,21 +48,22 @@ __device__ __forceinline__ void ld_pairs(const T* p, Pr<T>& a, Pr<T>& b) {
     b = mk(c.z, c.w);
 }
 
-// Up to 128 registers a thread: a lane holds R row pairs.
+// One 64-line tile (tile index = x-block + xblocks * outer) solved by the NW
+// warps of a CTA; raw is the CTA's dynamic shared memory (Cols2Smem bytes).
 template <typename T, int R, int NW, bool UPDATE>
-__global__ void __launch_bounds__(NW * 32, (512 / (NW * 32)) > 0 ? 512 / (NW * 32) : 1)
-ch_solve_cols2(T* __restrict__ a, T* __restrict__ Cf, int nx, int64_t outer_stride, int64_t line_stride,
-               CCoef<T> cf, unsigned int* status) {
+__device__ __forceinline__ void solve_cols2_tile(T* a, T* Cf, int nx, int64_t outer_stride, int64_t line_stride,
+                                                 const CCoef<T>& cf, unsigned int* status, int64_t tile,
+                                                 unsigned char* raw) {
     using SM = Cols2Smem<T, R, NW, UPDATE>;
-    extern __shared__ __align__(16) unsigned char cols2_raw[];
-    Pr<T>* fq = reinterpret_cast<Pr<T>*>(cols2_raw);       // [NW][2][32]
+    __syncthreads();  // the buffers may still be read by a previous tile of this CTA
+    Pr<T>* fq = reinterpret_cast<Pr<T>*>(raw);             // [NW][2][32]
     Pr<T>* bq = fq + NW * 2 * 32;                          // [NW][2][32]
     Pr<T>* wacc = bq + NW * 2 * 32;                        // [NW][4][32] (periodic)
     Pr<T>* cbuf = wacc + (cf.periodic ? NW * 4 * 32 : 0);  // [rows][32] (prefetched C)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int xblocks = (nx + 63) >> 6;
-    const int xb = blockIdx.x % xblocks;
-    const int64_t outer = blockIdx.x / xblocks;
+    const int xb = (int)(tile % xblocks);
+    const int64_t outer = tile / xblocks;
     const int ia = xb * 64 + 2 * lane;
     const bool valid = ia < nx;  // nx even: ia + 1 < nx as well
     const int n = cf.n;
@@ -202,6 +203,15 @@ ch_solve_cols2(T* __restrict__ a, T* __restrict__ Cf, int nx, int64_t outer_stri
         }
     }
     if (UPDATE && bad) atomicOr(status, 1u);
+}
+
+// Up to 128 registers a thread: a lane holds R row pairs.
+template <typename T, int R, int NW, bool UPDATE>
+__global__ void __launch_bounds__(NW * 32, (512 / (NW * 32)) > 0 ? 512 / (NW * 32) : 1)
+ch_solve_cols2(T* __restrict__ a, T* __restrict__ Cf, int nx, int64_t outer_stride, int64_t line_stride,
+               CCoef<T> cf, unsigned int* status) {
+    extern __shared__ __align__(16) unsigned char cols2_raw[];
+    solve_cols2_tile<T, R, NW, UPDATE>(a, Cf, nx, outer_stride, line_stride, cf, status, blockIdx.x, cols2_raw);
 }
 
 }  // namespace chg
