@@ -40,12 +40,25 @@ __device__ __forceinline__ void cp_async_pair(Pr<double>* dst, const double* src
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src) : "memory");
 }
 
+// Coefficient loads: volatile (issued in program order, so the compiler
+// does not keep R rows of coefficients live) unless CH_COLS2_PLAIN_LOADS.
+#ifndef CH_COLS2_PLAIN_LOADS
+#define CH_COLS2_PLAIN_LOADS 0
+#endif
+
 // two duplicated pairs (a, a, b, b) from a coefficient table row
 template <typename T>
 __device__ __forceinline__ void ld_pairs(const T* p, Pr<T>& a, Pr<T>& b) {
-    const V4<T> c = ldv4(p);
+    const V4<T> c = CH_COLS2_PLAIN_LOADS ? ld4(p) : ldv4(p);
     a = mk(c.x, c.y);
     b = mk(c.z, c.w);
+}
+template <typename T>
+__device__ __forceinline__ void ld_pair(const T* p, T& a, T& b) {
+    if (CH_COLS2_PLAIN_LOADS)
+        ld2(p, a, b);
+    else
+        ldv2(p, a, b);
 }
 
 // One 64-line tile (tile index = x-block + xblocks * outer) solved by the NW
@@ -146,7 +159,7 @@ __device__ __forceinline__ void solve_cols2_tile(T* a, T* Cf, int nx, int64_t ou
         y2 = y1;
         y1 = y;
         T d0, d1;
-        ldv2(cf.dinvp + 2 * (j0 + i), d0, d1);
+        ld_pair(cf.dinvp + 2 * (j0 + i), d0, d1);
         v[i] = mul(y, mk(d0, d1));
     }
     // back substitution from a zero state over this warp's rows

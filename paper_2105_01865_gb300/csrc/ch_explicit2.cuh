@@ -109,6 +109,9 @@ __device__ __forceinline__ Pr<T> face_flux_p(Pr<T> vel, Pr<T> m3, Pr<T> m2, Pr<T
 #ifndef CH_EXPLICIT_TZ
 #define CH_EXPLICIT_TZ 8
 #endif
+#ifndef CH_EXPLICIT_STAGE_OFFSETS
+#define CH_EXPLICIT_STAGE_OFFSETS 1
+#endif
 constexpr int kTX2 = 64;               // cells in x per CTA (two per thread)
 constexpr int kTZ2 = CH_EXPLICIT_TZ;   // z-planes marched per CTA
 constexpr int kHL2 = 4;   // left halo columns (even, so thread pairs stay 8/16-byte aligned)
@@ -177,6 +180,28 @@ __device__ __forceinline__ void explicit_tile2(const T* C, const T* u, const T* 
     }
     __syncthreads();  // index tables ready
 
+#if CH_EXPLICIT_STAGE_OFFSETS
+    // in-plane source offsets of this thread's staged elements e = tid + 256 m,
+    // the same for every plane of the tile
+    constexpr int kStageN = (PX * PY + 32 * kTY - 1) / (32 * kTY);
+    int soff[kStageN];
+#pragma unroll
+    for (int m = 0; m < kStageN; ++m) {
+        const int e = tid + m * 32 * kTY;
+        const int row = e / PX, cc = e - row * PX;
+        soff[m] = e < PX * PY ? gj_tab[row] * a.nx + gi_tab[cc] : 0;
+    }
+    auto stage = [&](int kk, int b) {
+        const T* Ck = C + (int64_t)kk * plane;
+        T* dst = &Cs[b][0][0];
+#pragma unroll
+        for (int m = 0; m < kStageN; ++m) {
+            const int e = tid + m * 32 * kTY;
+            if (e < PX * PY) cp_async_elem(dst + e, Ck + soff[m]);
+        }
+        cp_async_commit();
+    };
+#else
     auto stage = [&](int kk, int b) {
         const T* Ck = C + (int64_t)kk * plane;
         for (int e = tid; e < PX * PY; e += 32 * kTY) {
@@ -185,6 +210,7 @@ __device__ __forceinline__ void explicit_tile2(const T* C, const T* u, const T* 
         }
         cp_async_commit();
     };
+#endif
     stage(k0, 0);
     for (int k = k0, buf = 0; k < kend; ++k, buf = (buf == 2 ? 0 : buf + 1)) {
         if (k + 1 < kend) {
