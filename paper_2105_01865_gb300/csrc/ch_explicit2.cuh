@@ -137,8 +137,9 @@ __device__ __forceinline__ void explicit_tile2(const T* C, const T* u, const T* 
     const int ia = i0 + 2 * tx, j = j0 + ty;   // this thread's cells: (ia, j) and (ia + 1, j)
     const bool in_xy = (ia < a.nx) && (j < a.ny);
     const int ic = min(ia, a.nx - 2), jc = min(j, a.ny - 1);
-    const int64_t plane = (int64_t)a.nx * a.ny;
-    const int64_t col = (int64_t)jc * a.nx + ic;
+    // element indices fit in 32 bits (every extent <= 1024, so fields hold < 2^31 elements)
+    const int plane = a.nx * a.ny;
+    const int col = jc * a.nx + ic;
     const Pr<T> eps = sp<T>(a.eps);
     const int kend = min(k0 + zchunk, a.nz);
 
@@ -167,14 +168,14 @@ __device__ __forceinline__ void explicit_tile2(const T* C, const T* u, const T* 
     // z-column queue of pairs: q[m] = C(ia..ia+1, jc, k - 2 + m)
     Pr<T> q[6];
 #pragma unroll
-    for (int m = 0; m < 6; ++m) q[m] = ldp(C + (int64_t)bc_near(k0 - 2 + m, a.nz, a.bcz) * plane + col);
+    for (int m = 0; m < 6; ++m) q[m] = ldp(C + (bc_near(k0 - 2 + m, a.nz, a.bcz) * plane + col));
 
     Pr<T> fz_lo = sp<T>(T(0));
     if (ADV) {
         const bool wall = (a.bcz == CH_NOFLUX) && (k0 == 0);
         if (!wall) {
-            const Pr<T> cm3 = ldp(C + (int64_t)bc_near(k0 - 3, a.nz, a.bcz) * plane + col);
-            const Pr<T> wv = ldp(w + (int64_t)k0 * plane + col);
+            const Pr<T> cm3 = ldp(C + (bc_near(k0 - 3, a.nz, a.bcz) * plane + col));
+            const Pr<T> wv = ldp(w + (k0 * plane + col));
             fz_lo = face_flux_p(wv, cm3, q[0], q[1], q[2], q[3], q[4], eps);
         }
     }
@@ -192,7 +193,7 @@ __device__ __forceinline__ void explicit_tile2(const T* C, const T* u, const T* 
         soff[m] = e < PX * PY ? gj_tab[row] * a.nx + gi_tab[cc] : 0;
     }
     auto stage = [&](int kk, int b) {
-        const T* Ck = C + (int64_t)kk * plane;
+        const T* Ck = C + kk * plane;
         T* dst = &Cs[b][0][0];
 #pragma unroll
         for (int m = 0; m < kStageN; ++m) {
@@ -220,23 +221,23 @@ __device__ __forceinline__ void explicit_tile2(const T* C, const T* u, const T* 
             cp_async_wait<0>();
         }
         // per-thread global inputs of this plane (issued before the barrier)
-        const Pr<T> qnext = ldp(C + (int64_t)bc_near(k + 4, a.nz, a.bcz) * plane + col);
-        const int64_t kp = (int64_t)k * a.ny;
+        const Pr<T> qnext = ldp(C + (bc_near(k + 4, a.nz, a.bcz) * plane + col));
+        const int kp = k * a.ny;
         T uxa = T(0), uxb = T(0), uxe_a = T(0), uxe_b = T(0);
         Pr<T> vy = sp<T>(T(0)), vye = sp<T>(T(0)), wz = sp<T>(T(0)), hp = sp<T>(T(0));
         const bool zwall = (a.bcz == CH_NOFLUX) && (k + 1 >= a.nz);
         if (ADV) {
             uxa = wxa ? T(0) : u[(kp + jc) * a.nfx + fxa];
             uxb = wxb ? T(0) : u[(kp + jc) * a.nfx + fxb];
-            if (!wy) vy = ldp(v + ((int64_t)k * a.nfy + fy) * a.nx + ic);
-            if (ty == 0 && !wye) vye = ldp(v + ((int64_t)k * a.nfy + fye) * a.nx + ic);
+            if (!wy) vy = ldp(v + ((k * a.nfy + fy) * a.nx + ic));
+            if (ty == 0 && !wye) vye = ldp(v + ((k * a.nfy + fye) * a.nx + ic));
             if (ty == 1 && tx < 4 && !wxe) {
                 uxe_a = u[(kp + jea) * a.nfx + fxe];
                 uxe_b = u[(kp + jeb) * a.nfx + fxe];
             }
-            if (!zwall) wz = ldp(w + (int64_t)((k + 1 < a.nz) ? k + 1 : 0) * plane + col);
+            if (!zwall) wz = ldp(w + (((k + 1 < a.nz) ? k + 1 : 0) * plane + col));
         }
-        if (a.has_prev && in_xy) hp = ldp(Hprev + (int64_t)k * plane + (int64_t)j * a.nx + ia);
+        if (a.has_prev && in_xy) hp = ldp(Hprev + (k * plane + j * a.nx + ia));
         __syncthreads();
 
         const T(*P)[PX] = Cs[buf];
@@ -312,7 +313,7 @@ __device__ __forceinline__ void explicit_tile2(const T* C, const T* u, const T* 
             H = fma2(sp<T>(-a.inv_h), div, H);
         }
         if (in_xy) {
-            const int64_t idx = (int64_t)k * plane + (int64_t)j * a.nx + ia;
+            const int idx = k * plane + j * a.nx + ia;
             Pr<T> rhs = fma2(sp<T>(-a.impl), astar, mul(sp<T>(a.dtg), H));
             if (a.has_prev) rhs = fma2(sp<T>(a.dtr), hp, rhs);
             stp(Hout + idx, H);
