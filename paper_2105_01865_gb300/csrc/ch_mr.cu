@@ -153,12 +153,37 @@ __device__ __forceinline__ void load_w(const T* __restrict__ w, int i, T* out) {
     for (int m = 0; m < 4; ++m) out[m] = w[4 * i + m];
 }
 
+// Running sum of the integration (step 3).  FP32 keeps a compensation term
+// (Kahan's summation: the rounding error of every addition is carried and
+// fed back), so a 1024-term prefix sum stays within a few FP32 roundings of
+// the exact sum without FP64 arithmetic, which is slow on this GPU; FP64 sums
+// plainly.
+template <typename T>
+struct RunSum {
+    T s = T(0), c = T(0);  // sum and the negated lost low-order part
+    __device__ __forceinline__ void add(T x) {
+        const T y = __fsub_rn(x, c);
+        const T t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ T value() const { return __fsub_rn(s, c); }
+    __device__ __forceinline__ T plus(T x) const { return __fadd_rn(s, __fsub_rn(x, c)); }
+};
+template <>
+struct RunSum<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double value() const { return s; }
+    __device__ __forceinline__ double plus(double x) const { return s + x; }
+};
+
 // Step (3) along x: one warp per fine x-line (j, k).  The 64-point stencil
 // is sum-factorised: the warp first contracts the 16 coarse rows of its (y, z)
 // stencil into one coarse x-line g(ix) = sum_{b,c} wy_b wz_c G(ix, sy+b, sz+c)
 // (coalesced over ix, kept in shared memory), then every fine point needs only
 // its 4-point x-stencil of g.  u(face i) = u_ref(j, k) + h sum_{i' < i} Gx(i'),
-// the running sum kept in FP64 (warp scan with carry).
+// a warp scan per 32-point chunk plus a compensated carry (RunSum).
 constexpr int kMrWarps = 8;
 
 template <typename T>
@@ -196,10 +221,11 @@ mr_integrate_x(const T* __restrict__ gx, const T* __restrict__ uc, Tab<T> tx, Ta
     if (!a.wall[0]) uref = hermite2(uc, (int64_t)a.ncy * a.ncfx, (int64_t)a.ncfx, a.ncz, a.ncy, sz, wz, sy, wy);
     __syncwarp();
     T* row = u + ((int64_t)k * a.ny + j) * a.nfx;
-    double carry = 0.0;
+    const T hT = (T)a.h;
+    RunSum<T> carry;  // sum over the previous 32-point chunks
     for (int i0 = 0; i0 < a.nx; i0 += 32) {
         const int i = i0 + lane;
-        double gv = 0.0;
+        T gv = T(0);
         if (i < a.nx) {
             T wx[4];
             load_w(tx.w, i, wx);
@@ -211,18 +237,19 @@ mr_integrate_x(const T* __restrict__ gx, const T* __restrict__ uc, Tab<T> tx, Ta
                 kx -= (kx >= a.ncx) ? a.ncx : 0;
                 acc += wx[q] * g[kx];
             }
-            gv = (double)acc;
+            gv = acc;
         }
-        double incl = gv;
+        T incl = gv;  // inclusive scan of the chunk over lanes
         for (int o = 1; o < 32; o <<= 1) {
-            const double t = __shfl_up_sync(0xffffffffu, incl, o);
+            const T t = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += t;
         }
-        const double excl = carry + incl - gv;
-        if (i < a.nx) row[i] = uref + T(a.h * excl);
-        carry += __shfl_sync(0xffffffffu, incl, 31);
+        T excl = __shfl_up_sync(0xffffffffu, incl, 1);
+        if (lane == 0) excl = T(0);
+        if (i < a.nx) row[i] = uref + hT * carry.plus(excl);
+        carry.add(__shfl_sync(0xffffffffu, incl, 31));
     }
-    if (a.wall[0] && lane == 0) row[a.nx] = uref + T(a.h * carry);
+    if (a.wall[0] && lane == 0) row[a.nx] = uref + hT * carry.value();
 }
 
 // Contraction of a coarse gradient over the 4 x 4 stencil of the two
@@ -284,7 +311,8 @@ mr_integrate_yz(const T* __restrict__ G, const T* __restrict__ Vc, Tab<T> tx, Ta
     }
     T win[4];
     int ws = -1;  // coarse start index of the window
-    double run = 0.0;
+    const T hT = (T)a.h;
+    RunSum<T> run;
     for (int jl = 0; jl < nlong; ++jl) {
         const int sl = tl.s[jl];
         if (sl != ws) {
@@ -304,14 +332,14 @@ mr_integrate_yz(const T* __restrict__ G, const T* __restrict__ Vc, Tab<T> tx, Ta
         }
         T wl[4];
         load_w(tl.w, jl, wl);
-        const double gval = (double)(wl[0] * win[0] + wl[1] * win[1] + wl[2] * win[2] + wl[3] * win[3]);
+        const T gval = wl[0] * win[0] + wl[1] * win[1] + wl[2] * win[2] + wl[3] * win[3];
         const int64_t idx = DIR == 1 ? ((int64_t)o * a.nfy + jl) * a.nx + i : ((int64_t)jl * a.ny + o) * a.nx + i;
-        out[idx] = ref + T(a.h * run);
-        run += gval;
+        out[idx] = ref + hT * run.value();
+        run.add(gval);
     }
     if (a.wall[DIR]) {
         const int64_t idx = DIR == 1 ? ((int64_t)o * a.nfy + a.ny) * a.nx + i : ((int64_t)a.nz * a.ny + o) * a.nx + i;
-        out[idx] = ref + T(a.h * run);
+        out[idx] = ref + hT * run.value();
     }
 }
 
