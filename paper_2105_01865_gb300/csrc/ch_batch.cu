@@ -574,6 +574,7 @@ int ch_batch_create(const ch_params* boxes, int nbox, void* const* C, void* work
                         c.bwdp = base + L.bwdp;
                         c.Wp = base + L.Wp;
                         c.Zp = base + L.Zp;
+                        c.K = base + L.K;
                         c.n = nd;
                         c.periodic = per;
                         off += align256(t.size() * sizeof(float));

@@ -23,12 +23,12 @@ template <typename T, int R, int NW, bool UPDATE>
 struct Cols2Smem {
     static constexpr size_t kPair = 2 * sizeof(T);
     static constexpr size_t kQueues = (size_t)NW * 2 * 32 * kPair * 2;  // forward + backward chunk states
-    static constexpr size_t kWacc = (size_t)NW * 4 * 32 * kPair;        // periodic only
+    static constexpr size_t kCorner = (size_t)4 * 32 * kPair;           // corner rows (periodic)
     static constexpr size_t kRows = (size_t)NW * R;
     static constexpr bool kPrefetch = UPDATE && kRows * 32 * kPair <= 96 * 1024;
     static constexpr size_t kCbuf = kPrefetch ? kRows * 32 * kPair : 0;
-    static constexpr size_t bytes(bool periodic) { return kQueues + (periodic ? kWacc : 0) + kCbuf; }
-    static constexpr size_t kMax = kQueues + kWacc + kCbuf;
+    static constexpr size_t bytes(bool) { return kQueues + kCorner + kCbuf; }
+    static constexpr size_t kMax = kQueues + kCorner + kCbuf;
 };
 
 __device__ __forceinline__ void cp_async_pair(Pr<float>* dst, const float* src) {
@@ -69,10 +69,10 @@ __device__ __forceinline__ void solve_cols2_tile(T* a, T* Cf, int nx, int64_t ou
                                                  unsigned char* raw) {
     using SM = Cols2Smem<T, R, NW, UPDATE>;
     __syncthreads();  // the buffers may still be read by a previous tile of this CTA
-    Pr<T>* fq = reinterpret_cast<Pr<T>*>(raw);             // [NW][2][32]
-    Pr<T>* bq = fq + NW * 2 * 32;                          // [NW][2][32]
-    Pr<T>* wacc = bq + NW * 2 * 32;                        // [NW][4][32] (periodic)
-    Pr<T>* cbuf = wacc + (cf.periodic ? NW * 4 * 32 : 0);  // [rows][32] (prefetched C)
+    Pr<T>* fq = reinterpret_cast<Pr<T>*>(raw);  // [NW][2][32]
+    Pr<T>* bq = fq + NW * 2 * 32;               // [NW][2][32]
+    Pr<T>* corner = bq + NW * 2 * 32;           // [4][32] (periodic)
+    Pr<T>* cbuf = corner + 4 * 32;              // [rows][32] (prefetched C)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int xblocks = (nx + 63) >> 6;
     const int xb = (int)(tile % xblocks);
@@ -97,7 +97,6 @@ __device__ __forceinline__ void solve_cols2_tile(T* a, T* Cf, int nx, int64_t ou
 
     // forward elimination from a zero state over this warp's rows
     Pr<T> y1 = sp<T>(T(0)), y2 = sp<T>(T(0));
-    Pr<T> acc0 = sp<T>(T(0)), acc1 = acc0, acc2 = acc0, acc3 = acc0;
 #pragma unroll
     for (int i = 0; i < R; ++i) {
         Pr<T> nl1, nl2;
@@ -105,24 +104,9 @@ __device__ __forceinline__ void solve_cols2_tile(T* a, T* Cf, int nx, int64_t ou
         const Pr<T> y = fma2(nl1, y1, fma2(nl2, y2, v[i]));
         y2 = y1;
         y1 = y;
-        if (per) {
-            Pr<T> w0, w1, w2, w3;
-            ld_pairs(cf.Wp + 8 * (j0 + i), w0, w1);
-            ld_pairs(cf.Wp + 8 * (j0 + i) + 4, w2, w3);
-            acc0 = fma2(w0, v[i], acc0);
-            acc1 = fma2(w1, v[i], acc1);
-            acc2 = fma2(w2, v[i], acc2);
-            acc3 = fma2(w3, v[i], acc3);
-        }
     }
     fq[(w * 2 + 0) * 32 + lane] = y1;
     fq[(w * 2 + 1) * 32 + lane] = y2;
-    if (per) {
-        wacc[(w * 4 + 0) * 32 + lane] = acc0;
-        wacc[(w * 4 + 1) * 32 + lane] = acc1;
-        wacc[(w * 4 + 2) * 32 + lane] = acc2;
-        wacc[(w * 4 + 3) * 32 + lane] = acc3;
-    }
     __syncthreads();
     // incoming state: compose the chunks of warps 0 .. w-1
     Pr<T> s0 = sp<T>(T(0)), s1 = sp<T>(T(0));
@@ -132,22 +116,6 @@ __device__ __forceinline__ void solve_cols2_tile(T* a, T* Cf, int nx, int64_t ou
         const Pr<T> n1 = fma2(sp<T>(Pm.z), s0, fma2(sp<T>(Pm.w), s1, fq[(u * 2 + 1) * 32 + lane]));
         s0 = n0;
         s1 = n1;
-    }
-    Pr<T> sv0 = sp<T>(T(0)), sv1 = sv0, sv2 = sv0, sv3 = sv0;
-    if (per) {
-        Pr<T> t0 = sp<T>(T(0)), t1 = t0, t2 = t0, t3 = t0;
-#pragma unroll
-        for (int u = 0; u < NW; ++u) {
-            t0 = add(t0, wacc[(u * 4 + 0) * 32 + lane]);
-            t1 = add(t1, wacc[(u * 4 + 1) * 32 + lane]);
-            t2 = add(t2, wacc[(u * 4 + 2) * 32 + lane]);
-            t3 = add(t3, wacc[(u * 4 + 3) * 32 + lane]);
-        }
-        const V4<T> r0 = ld4(cf.S), r1 = ld4(cf.S + 4), r2 = ld4(cf.S + 8), r3 = ld4(cf.S + 12);
-        sv0 = fma2(sp<T>(r0.x), t0, fma2(sp<T>(r0.y), t1, fma2(sp<T>(r0.z), t2, mul(sp<T>(r0.w), t3))));
-        sv1 = fma2(sp<T>(r1.x), t0, fma2(sp<T>(r1.y), t1, fma2(sp<T>(r1.z), t2, mul(sp<T>(r1.w), t3))));
-        sv2 = fma2(sp<T>(r2.x), t0, fma2(sp<T>(r2.y), t1, fma2(sp<T>(r2.z), t2, mul(sp<T>(r2.w), t3))));
-        sv3 = fma2(sp<T>(r3.x), t0, fma2(sp<T>(r3.y), t1, fma2(sp<T>(r3.z), t2, mul(sp<T>(r3.w), t3))));
     }
     y1 = s0;
     y2 = s1;
@@ -187,8 +155,6 @@ __device__ __forceinline__ void solve_cols2_tile(T* a, T* Cf, int nx, int64_t ou
     }
     x1 = s0;
     x2 = s1;
-    bool bad = false;
-    T* dst = (UPDATE ? Cf : a) + g;
 #pragma unroll
     for (int i = R - 1; i >= 0; --i) {
         Pr<T> nu1, nu2;
@@ -196,7 +162,30 @@ __device__ __forceinline__ void solve_cols2_tile(T* a, T* Cf, int nx, int64_t ou
         const Pr<T> x = fma2(nu1, x1, fma2(nu2, x2, v[i]));
         x2 = x1;
         x1 = x;
-        Pr<T> o = x;
+        v[i] = x;
+        if (per) {  // corner rows 0, 1 -> slots 0, 1; rows n-2, n-1 -> slots 2, 3
+            const int j = j0 + i;
+            if (j < 2) corner[j * 32 + lane] = x;
+            else if (j >= n - 2 && j < n) corner[(j - n + 4) * 32 + lane] = x;
+        }
+    }
+    // periodic: the Woodbury correction from the corner rows (0, 1, n-2, n-1)
+    // of the banded solution, s = K y_c, then x -= Z s
+    Pr<T> sv0 = sp<T>(T(0)), sv1 = sv0, sv2 = sv0, sv3 = sv0;
+    if (per) {
+        __syncthreads();
+        const Pr<T> c0 = corner[lane], c1 = corner[32 + lane], c2 = corner[64 + lane], c3 = corner[96 + lane];
+        const V4<T> k0 = ld4(cf.K), k1 = ld4(cf.K + 4), k2 = ld4(cf.K + 8), k3 = ld4(cf.K + 12);
+        sv0 = fma2(sp<T>(k0.x), c0, fma2(sp<T>(k0.y), c1, fma2(sp<T>(k0.z), c2, mul(sp<T>(k0.w), c3))));
+        sv1 = fma2(sp<T>(k1.x), c0, fma2(sp<T>(k1.y), c1, fma2(sp<T>(k1.z), c2, mul(sp<T>(k1.w), c3))));
+        sv2 = fma2(sp<T>(k2.x), c0, fma2(sp<T>(k2.y), c1, fma2(sp<T>(k2.z), c2, mul(sp<T>(k2.w), c3))));
+        sv3 = fma2(sp<T>(k3.x), c0, fma2(sp<T>(k3.y), c1, fma2(sp<T>(k3.z), c2, mul(sp<T>(k3.w), c3))));
+    }
+    bool bad = false;
+    T* dst = (UPDATE ? Cf : a) + g;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        Pr<T> o = v[i];
         if (per) {
             Pr<T> z0, z1, z2, z3;
             ld_pairs(cf.Zp + 8 * (j0 + i), z0, z1);

@@ -719,6 +719,7 @@ struct CCoef {
     const T* __restrict__ bwdp;   // [rows][4]: -u1/u0 (x2), -u2/u0 (x2)
     const T* __restrict__ Wp;     // [rows][8]: W_m (x2), periodic only
     const T* __restrict__ Zp;     // [rows][8]: -Z_m (x2), periodic only
+    const T* __restrict__ K;      // [4][4] corner-form correction, periodic only
     int n;
     int periodic;
 };

@@ -173,6 +173,7 @@ CCoef<T> ccoef(const LineTables& lt) {
     k.bwdp = b + L.bwdp;
     k.Wp = b + L.Wp;
     k.Zp = b + L.Zp;
+    k.K = b + L.K;
     k.n = lt.n;
     k.periodic = lt.periodic;
     return k;

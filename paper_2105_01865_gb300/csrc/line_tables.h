@@ -87,6 +87,9 @@ struct LineFactors {
     std::vector<double> l1, l2, dinv, u1s, u2s;
     std::vector<double> W, Z;  // n x 4 each (periodic)
     double S[16] = {0};
+    // corner form of the correction: s = K y_c with y_c = (Mb^-1 r) at rows
+    // (0, 1, n-2, n-1), K = S V_c (V^T restricted to those columns)
+    double K[16] = {0};
     bool ok = false;
 };
 
@@ -172,6 +175,14 @@ inline LineFactors line_factors(int n, int bc, double ck) {
             cap[p * 4 + q] = s;
         }
     F.ok = invert4(cap, F.S);
+    // V^T y only reads y at the corner rows: K = S V_c
+    const int cols[4] = {0, 1, n - 2, n - 1};
+    for (int p = 0; p < 4; ++p)
+        for (int q = 0; q < 4; ++q) {
+            double acc = 0.0;
+            for (int m = 0; m < 4; ++m) acc += F.S[p * 4 + m] * Vt[(size_t)m * n + cols[q]];
+            F.K[p * 4 + q] = acc;
+        }
     return F;
 }
 
@@ -289,6 +300,7 @@ namespace chg {
 struct ColLayout {
     size_t fwd, bwd, W, Z, P, Q, S;
     size_t fwdp, dinvp, bwdp, Wp, Zp;  // the same rows as duplicated pairs (two-column form)
+    size_t K;                          // corner-form correction matrix (two-column form)
     size_t total;
 };
 
@@ -308,6 +320,7 @@ inline ColLayout col_layout(int nw, int R) {
     L.bwdp = off;  off += rows * 4;
     L.Wp = off;    off += rows * 8;
     L.Zp = off;    off += rows * 8;
+    L.K = off;     off += 16;
     L.total = (off + 63) / 64 * 64;
     return L;
 }
@@ -358,7 +371,10 @@ inline std::vector<double> col_tables(const LineFactors& F, int nw, int R) {
         }
     }
     if (F.periodic)
-        for (int m = 0; m < 16; ++m) t[L.S + m] = F.S[m];
+        for (int m = 0; m < 16; ++m) {
+            t[L.S + m] = F.S[m];
+            t[L.K + m] = F.K[m];
+        }
     return t;
 }
 
