@@ -213,6 +213,8 @@ __global__ void __launch_bounds__(NW * 32, (512 / (NW * 32)) > 0 ? 512 / (NW * 3
 ch_solve_cols2(T* __restrict__ a, T* __restrict__ Cf, int nx, int64_t outer_stride, int64_t line_stride,
                CCoef<T> cf, unsigned int* status) {
     extern __shared__ __align__(16) unsigned char cols2_raw[];
+    pdl_wait();
+    pdl_launch_dependents();
     solve_cols2_tile<T, R, NW, UPDATE>(a, Cf, nx, outer_stride, line_stride, cf, status, blockIdx.x, cols2_raw);
 }
 

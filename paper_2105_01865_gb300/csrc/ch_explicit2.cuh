@@ -374,6 +374,8 @@ __global__ void __launch_bounds__(32 * kTY, sizeof(T) == 4 ? CH_EXPLICIT_MIN_BLO
 ch_explicit_rhs2(const T* __restrict__ C, const T* __restrict__ u, const T* __restrict__ v,
                  const T* __restrict__ w, const T* __restrict__ Hprev, T* __restrict__ Hout, T* __restrict__ r,
                  RhsArgs<T> a) {
+    pdl_wait();
+    pdl_launch_dependents();
     explicit_tile2<T, ADV>(C, u, v, w, Hprev, Hout, r, a, blockIdx.x, blockIdx.y, blockIdx.z, kTZ2);
 }
 

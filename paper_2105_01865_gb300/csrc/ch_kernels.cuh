@@ -100,6 +100,15 @@ __device__ __forceinline__ T face_flux(T vel, T m3, T m2, T m1, T p0, T p1, T p2
     return vel * weno5(a1, a2, a3, a4, a5, eps);
 }
 
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialisation may be scheduled while its predecessor drains; pdl_wait()
+// blocks until the predecessor grid has completed and its writes are
+// visible, so every such kernel calls it before touching global memory.
+// pdl_launch_dependents() lets the next kernel be scheduled once every CTA of
+// this grid has started.  Both are no-ops for an ordinary launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Asynchronous global -> shared copies (cp.async): one element, 4 or 8 bytes.
 __device__ __forceinline__ void cp_async_elem(float* smem, const float* gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -129,6 +138,8 @@ __global__ void __launch_bounds__(kTX * kTY)
 ch_explicit_rhs(const T* __restrict__ C, const T* __restrict__ u, const T* __restrict__ v,
                 const T* __restrict__ w, const T* __restrict__ Hprev, T* __restrict__ Hout,
                 T* __restrict__ r, RhsArgs<T> a) {
+    pdl_wait();
+    pdl_launch_dependents();
     constexpr int PX = kTX + 2 * kHalo, PY = kTY + 2 * kHalo;
     __shared__ __align__(16) T Cs[3][PY][PX];
     __shared__ T Fx[ADV ? kTY : 1][kTX + 1];
@@ -604,6 +615,8 @@ __device__ __forceinline__ void solve_x_line(T* a, int64_t line, int nx, const W
 template <typename T, int M>
 __global__ void __launch_bounds__(256)
 ch_solve_x(T* __restrict__ a, int64_t nlines, int nx, WCoef<T> cf) {
+    pdl_wait();
+    pdl_launch_dependents();
     constexpr int L = LinesPerWarp<T, M>::value;
     const int64_t line0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * L;
     if (line0 >= nlines) return;  // whole warp
@@ -691,6 +704,8 @@ __global__ void __launch_bounds__(YZShape<T, M>::kWarps * 32, YZShape<T, M>::kMi
 ch_solve_yz(T* __restrict__ a, T* __restrict__ Cf, int nx, int64_t outer_stride, int64_t line_stride,
             WCoef<T> cf, unsigned int* status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_wait();
+    pdl_launch_dependents();
     solve_yz_tile<T, M, UPDATE, YZShape<T, M>::kWarps>(a, Cf, nx, outer_stride, line_stride, cf, status, blockIdx.x,
                                                         reinterpret_cast<T*>(smem_raw));
 }
@@ -751,6 +766,8 @@ template <typename T, int R, int NW, bool UPDATE>
 __global__ void __launch_bounds__(NW * 32, 1024 / (NW * 32))
 ch_solve_cols(T* __restrict__ a, T* __restrict__ Cf, int nx, int64_t outer_stride, int64_t line_stride, CCoef<T> cf,
               unsigned int* status) {
+    pdl_wait();
+    pdl_launch_dependents();
     __shared__ T fq[NW][2][32];
     __shared__ T bq[NW][2][32];
     __shared__ T wacc[NW][4][32];

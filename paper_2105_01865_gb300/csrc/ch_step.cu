@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <tuple>
+#include <utility>
 #include <vector>
 
 #include "ch_internal.h"
@@ -23,6 +24,30 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr size_t kMaxSmem = 227 * 1024;  // dynamic shared memory per CTA (sm_103a)
+
+// Launch a step kernel, optionally with programmatic stream serialisation
+// (CH_PDL = 1): it may then be scheduled while its predecessor on the stream
+// drains, and waits (pdl_wait) before touching memory.  Off by default: on the
+// shear-drop step the early CTAs slowed the predecessors' tails more than the
+// launch gaps they hide (0.628 against 0.619 ms per step).
+#ifndef CH_PDL
+#define CH_PDL 0
+#endif
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(cudaStream_t st, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                     Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = CH_PDL;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 bool params_valid(const ch_params* p, char* why, size_t wl) {
@@ -137,18 +162,18 @@ int launch_solves_m(ch_handle* h, int l, int dir, T* r, T* Cupd, cudaEvent_t ev_
     if (dir == 0) {
         const int64_t nlines = (int64_t)ny * nz;
         constexpr int wpb = 8, lpb = wpb * LinesPerWarp<T, M>::value;
-        ch_solve_x<T, M><<<(unsigned)((nlines + lpb - 1) / lpb), wpb * 32, 0, h->stream>>>(r, nlines, nx, cf);
+        launch_k(h->stream, ch_solve_x<T, M>, dim3((unsigned)((nlines + lpb - 1) / lpb)), dim3(wpb * 32), 0, r, nlines, nx, cf);
     } else {
         const unsigned xblocks = (unsigned)((nx + 31) / 32);
         const size_t shm = (size_t)32 * M * 32 * sizeof(T);
         if (dir == 1)
-            ch_solve_yz<T, M, false><<<xblocks * (unsigned)nz, YZShape<T, M>::kWarps * 32, shm, h->stream>>>(
+            launch_k(h->stream, ch_solve_yz<T, M, false>, dim3(xblocks * (unsigned)nz), dim3(YZShape<T, M>::kWarps * 32), shm,
                 r, nullptr, nx, (int64_t)nx * ny, nx, cf, h->status);
         else if (Cupd)
-            ch_solve_yz<T, M, true><<<xblocks * (unsigned)ny, YZShape<T, M>::kWarps * 32, shm, h->stream>>>(
+            launch_k(h->stream, ch_solve_yz<T, M, true>, dim3(xblocks * (unsigned)ny), dim3(YZShape<T, M>::kWarps * 32), shm,
                 r, Cupd, nx, nx, (int64_t)nx * ny, cf, h->status);
         else
-            ch_solve_yz<T, M, false><<<xblocks * (unsigned)ny, YZShape<T, M>::kWarps * 32, shm, h->stream>>>(
+            launch_k(h->stream, ch_solve_yz<T, M, false>, dim3(xblocks * (unsigned)ny), dim3(YZShape<T, M>::kWarps * 32), shm,
                 r, nullptr, nx, nx, (int64_t)nx * ny, cf, h->status);
     }
     CHG_CUDA(h, cudaGetLastError());
@@ -185,13 +210,13 @@ int launch_cols_rn(ch_handle* h, int l, int dir, T* r, T* Cupd) {
     const CCoef<T> cf = ccoef<T>(h->lines[dir][l]);
     const unsigned xblocks = (unsigned)((nx + 31) / 32);
     if (dir == 1)
-        ch_solve_cols<T, R, NW, false><<<xblocks * (unsigned)nz, NW * 32, 0, h->stream>>>(
+        launch_k(h->stream, ch_solve_cols<T, R, NW, false>, dim3(xblocks * (unsigned)nz), dim3(NW * 32), 0,
             r, nullptr, nx, (int64_t)nx * ny, nx, cf, h->status);
     else if (Cupd)
-        ch_solve_cols<T, R, NW, true><<<xblocks * (unsigned)ny, NW * 32, 0, h->stream>>>(
+        launch_k(h->stream, ch_solve_cols<T, R, NW, true>, dim3(xblocks * (unsigned)ny), dim3(NW * 32), 0,
             r, Cupd, nx, nx, (int64_t)nx * ny, cf, h->status);
     else
-        ch_solve_cols<T, R, NW, false><<<xblocks * (unsigned)ny, NW * 32, 0, h->stream>>>(
+        launch_k(h->stream, ch_solve_cols<T, R, NW, false>, dim3(xblocks * (unsigned)ny), dim3(NW * 32), 0,
             r, nullptr, nx, nx, (int64_t)nx * ny, cf, h->status);
     CHG_CUDA(h, cudaGetLastError());
     return CH_OK;
@@ -205,16 +230,13 @@ int launch_cols2_rn(ch_handle* h, int l, int dir, T* r, T* Cupd) {
     const unsigned xblocks = (unsigned)((nx + 63) / 64);
     const bool per = cf.periodic != 0;
     if (dir == 1) {
-        ch_solve_cols2<T, R, NW, false><<<xblocks * (unsigned)nz, NW * 32,
-                                          Cols2Smem<T, R, NW, false>::bytes(per), h->stream>>>(
+        launch_k(h->stream, ch_solve_cols2<T, R, NW, false>, dim3(xblocks * (unsigned)nz), dim3(NW * 32), Cols2Smem<T, R, NW, false>::bytes(per),
             r, nullptr, nx, (int64_t)nx * ny, nx, cf, h->status);
     } else if (Cupd) {
-        ch_solve_cols2<T, R, NW, true><<<xblocks * (unsigned)ny, NW * 32,
-                                         Cols2Smem<T, R, NW, true>::bytes(per), h->stream>>>(
+        launch_k(h->stream, ch_solve_cols2<T, R, NW, true>, dim3(xblocks * (unsigned)ny), dim3(NW * 32), Cols2Smem<T, R, NW, true>::bytes(per),
             r, Cupd, nx, nx, (int64_t)nx * ny, cf, h->status);
     } else {
-        ch_solve_cols2<T, R, NW, false><<<xblocks * (unsigned)ny, NW * 32,
-                                          Cols2Smem<T, R, NW, false>::bytes(per), h->stream>>>(
+        launch_k(h->stream, ch_solve_cols2<T, R, NW, false>, dim3(xblocks * (unsigned)ny), dim3(NW * 32), Cols2Smem<T, R, NW, false>::bytes(per),
             r, nullptr, nx, nx, (int64_t)nx * ny, cf, h->status);
     }
     CHG_CUDA(h, cudaGetLastError());
@@ -363,16 +385,16 @@ int launch_explicit(ch_handle* h, int l, const T* C, const T* Hprev, T* Hout, T*
         dim3 grid((nx + kTX2 - 1) / kTX2, (ny + kTY - 1) / kTY, (nz + kTZ2 - 1) / kTZ2);
         dim3 block(32, kTY);
         if (p.advect)
-            ch_explicit_rhs2<T, true><<<grid, block, 0, h->stream>>>(C, u, v, w, Hprev, Hout, r, a);
+            launch_k(h->stream, ch_explicit_rhs2<T, true>, dim3(grid), dim3(block), 0, C, u, v, w, Hprev, Hout, r, a);
         else
-            ch_explicit_rhs2<T, false><<<grid, block, 0, h->stream>>>(C, u, v, w, Hprev, Hout, r, a);
+            launch_k(h->stream, ch_explicit_rhs2<T, false>, dim3(grid), dim3(block), 0, C, u, v, w, Hprev, Hout, r, a);
     } else {
         dim3 grid((nx + kTX - 1) / kTX, (ny + kTY - 1) / kTY, (nz + kTZ - 1) / kTZ);
         dim3 block(kTX, kTY);
         if (p.advect)
-            ch_explicit_rhs<T, true><<<grid, block, 0, h->stream>>>(C, u, v, w, Hprev, Hout, r, a);
+            launch_k(h->stream, ch_explicit_rhs<T, true>, dim3(grid), dim3(block), 0, C, u, v, w, Hprev, Hout, r, a);
         else
-            ch_explicit_rhs<T, false><<<grid, block, 0, h->stream>>>(C, u, v, w, Hprev, Hout, r, a);
+            launch_k(h->stream, ch_explicit_rhs<T, false>, dim3(grid), dim3(block), 0, C, u, v, w, Hprev, Hout, r, a);
     }
     CHG_CUDA(h, cudaGetLastError());
     if (ev) CHG_CUDA(h, cudaEventRecord(ev[1], h->stream));
