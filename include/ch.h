@@ -104,9 +104,12 @@ size_t ch_workspace_bytes(const ch_params* p);
  * stream: cudaStream_t for all work.  Builds the LU factors of the line
  * operators (I + (alpha_l dt M / 2) A_d) for the three RK3 substeps, and with
  * a coarse mesh the Hermite index/weight tables (Sec. 3.4: the tables are built
- * once per mesh pair).  Errors: CH_EINVAL (sizes < 5, non-positive h/cn/pe/dt/w, bad bc,
- * coarse faces not spanning the fine box, misaligned pointers), CH_ENOMEM,
- * CH_ECUDA.  On success *out owns the tables until ch_free. */
+ * once per mesh pair).  nz = 1 with a periodic z is a single plane: the 2D
+ * scheme of Sec. 3.1 (A_x + A_y; Eq. eq-a2d is w = 2), with no z-solve.
+ * Errors: CH_EINVAL (nx or ny < 5, nz < 5 other than that single plane,
+ * non-positive h/cn/pe/dt/w, bad bc, coarse faces not spanning the fine box, a
+ * coarse mesh with nz < 5, misaligned pointers), CH_ENOMEM, CH_ECUDA.  On
+ * success *out owns the tables until ch_free. */
 int ch_create(const ch_params* p, void* C, void* work, size_t work_bytes, void* stream, ch_handle** out);
 
 /* Release the library-owned tables and the handle (not C or the workspace). */

@@ -58,6 +58,7 @@ __device__ __forceinline__ int bc_index(int i, int n, int bc) {
 // The same rule for indices at most one period outside [0, n) (n >= 5 and
 // offsets of at most 4), without division.
 __device__ __forceinline__ int bc_near(int i, int n, int bc) {
+    if (n == 1) return 0;  // a single periodic plane: every neighbour is the plane itself
     if (i < 0) return bc == CH_PERIODIC ? i + n : -1 - i;
     if (i >= n) return bc == CH_PERIODIC ? i - n : 2 * n - 1 - i;
     return i;
@@ -897,6 +898,20 @@ ch_solve_cols(T* __restrict__ a, T* __restrict__ Cf, int nx, int64_t outer_strid
         }
     }
     if (UPDATE && bad) atomicOr(status, 1u);
+}
+
+// C += dq for a single-plane (2D) box, which has no z-solve to fuse it into;
+// non-finite results raise the status flag.
+template <typename T>
+__global__ void __launch_bounds__(256) ch_add_increment(T* __restrict__ C, const T* __restrict__ dq, int64_t N,
+                                                        unsigned int* status) {
+    bool bad = false;
+    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < N; e += (int64_t)gridDim.x * 256) {
+        const T c = C[e] + dq[e];
+        bad |= !isfinite(c);
+        C[e] = c;
+    }
+    if (bad) atomicOr(status, 1u);
 }
 
 // ---------------------------------------------------------------------------

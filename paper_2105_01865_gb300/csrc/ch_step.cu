@@ -56,7 +56,10 @@ bool params_valid(const ch_params* p, char* why, size_t wl) {
         return false;
     };
     if (!p) return bad("params is NULL");
-    if (p->nx < 5 || p->ny < 5 || p->nz < 5) return bad("nx, ny, nz must each be >= 5");
+    if (p->nx < 5 || p->ny < 5) return bad("nx and ny must each be >= 5");
+    // nz = 1 with a periodic z: one plane, the 2D scheme (A_x + A_y, Eq. eq-a2d with w = 2)
+    if (p->nz < 5 && !(p->nz == 1 && p->bc[2] == CH_PERIODIC))
+        return bad("nz must be >= 5, or 1 (a periodic single plane: the 2D scheme)");
     if (p->nx > (1 << 20) || p->ny > (1 << 20) || p->nz > (1 << 20)) return bad("a dimension exceeds 2^20");
     if ((double)p->nx * p->ny * p->nz > 9.0e18 / 8) return bad("grid too large");
     if (!(p->h > 0) || !(p->cn > 0) || !(p->pe > 0) || !(p->dt > 0) || !(p->w > 0) || !(p->weno_eps > 0))
@@ -73,6 +76,7 @@ bool params_valid(const ch_params* p, char* why, size_t wl) {
     const bool any_c = p->ncx || p->ncy || p->ncz || p->xf_coarse || p->yf_coarse || p->zf_coarse;
     if (any_c) {
         if (p->ncx < 4 || p->ncy < 4 || p->ncz < 4) return bad("coarse mesh needs >= 4 cells per direction");
+        if (p->nz < 5) return bad("a coarse mesh needs nz >= 5");
         if (p->ncx > kMaxCoarseLine || p->ncy > kMaxCoarseLine || p->ncz > kMaxCoarseLine)
             return bad("coarse mesh has more than 2048 cells in a direction");
         if (!p->xf_coarse || !p->yf_coarse || !p->zf_coarse) return bad("coarse face coordinates missing");
@@ -408,8 +412,17 @@ int launch_substep(ch_handle* h, int l, cudaEvent_t* ev = nullptr) {
     T* r = (T*)h->r;
     int rc = launch_explicit<T>(h, l, C, (const T*)h->H[(l + 1) & 1], (T*)h->H[l & 1], r, ev);
     if (rc != CH_OK) return rc;
-    // x solve (Eq. eq-fac-1), y solve (Eq. eq-fac-2), z solve + update (Eq. eq-fac-3)
+    // x solve (Eq. eq-fac-1), y solve (Eq. eq-fac-2), z solve + update (Eq. eq-fac-3);
+    // a single plane (2D scheme) has no z-solve: C += dq directly
     for (int dir = 0; dir < 3; ++dir) {
+        if (dir == 2 && h->n[2] == 1) {
+            const int64_t N = h->ncell;
+            const unsigned blocks = (unsigned)std::min<int64_t>((N + 255) / 256, 16 * 152);
+            ch_add_increment<T><<<blocks, 256, 0, h->stream>>>(C, r, N, h->status);
+            CHG_CUDA(h, cudaGetLastError());
+            if (ev) CHG_CUDA(h, cudaEventRecord(ev[4], h->stream));
+            continue;
+        }
         rc = launch_solve<T>(h, l, dir, r, dir == 2 ? C : nullptr, ev ? ev[2 + dir] : nullptr);
         if (rc != CH_OK) return rc;
     }
@@ -551,6 +564,16 @@ int ch_create(const ch_params* p, void* C, void* work, size_t work_bytes, void* 
             for (int l = 0; l < kRK; ++l) {
                 const double ck = (kGamma[l] + kRho[l]) * p->dt * M / 2.0 * kappa;
                 const int n = (int)h->n[d];
+                if (n == 1) {  // a single periodic z-plane (2D scheme): no z-solve
+                    LineTables& lt = h->lines[d][l];
+                    lt.n = 1;
+                    lt.M = 1;
+                    lt.periodic = 1;
+                    lt.nw = lt.R = 0;
+                    all.push_back({});
+                    all.push_back({});
+                    continue;
+                }
                 const LineFactors F = line_factors(n, p->bc[d], ck);
                 if (!F.ok) {
                     free(h);
