@@ -330,6 +330,40 @@ def step_standard(C, vel, p: Params, nsteps=1, psi_p=psi_prime):
 
 
 # ---------------------------------------------------------------------------
+# Back-coupling quantities of Sec. 2.2 (Eqs. eq-rho, eq-mu, eq-fst)
+# ---------------------------------------------------------------------------
+
+def chemical_potential(C, p: Params):
+    """phi = psi'(C) - Cn^2 lap_h C, the bracket of Eq. (eq-ch)."""
+    return psi_prime(C) - p.cn ** 2 * lap_h(C, p)
+
+
+def grad_c(C, p: Params, d):
+    """Central difference (C_{+d} - C_{-d}) / (2h) along d, with the ghost
+    cells of lap_h (wrap, or the mirror about a wall face)."""
+    Cp = pad(C, p.bc, 1)
+    return (shifted(Cp, 1, d, 1, p.shape) - shifted(Cp, 1, d, -1, p.shape)) / (2.0 * p.h)
+
+
+def surface_tension(C, p: Params):
+    """F_st = 6 sqrt(2) phi grad C / Cn at the fine cell centres (Eq. eq-fst,
+    with phi the chemical potential); returns the (x, y, z) components."""
+    phi = chemical_potential(C, p)
+    k = 6.0 * np.sqrt(2.0) / p.cn
+    return tuple(k * phi * grad_c(C, p, d) for d in range(3))
+
+
+def density(C, lam_rho):
+    """rho = C + lambda_rho (1 - C), Eq. (eq-rho)."""
+    return C + lam_rho * (1.0 - C)
+
+
+def viscosity(C, lam_mu):
+    """mu = C + lambda_mu (1 - C), Eq. (eq-mu)."""
+    return C + lam_mu * (1.0 - C)
+
+
+# ---------------------------------------------------------------------------
 # Diagnostics: mass (Sec. 4.3, l_loss) and free energy (Sec. 1)
 # ---------------------------------------------------------------------------
 

@@ -16,6 +16,13 @@ transferred to the uniform fine mesh of C by
 Because the three gradients share the same tensor-product weights, the fine
 discrete divergence equals the interpolated coarse divergence.
 
+The back-coupling of C (Sec. 3.4, last step) projects the fine field directly
+to the stretched mesh; ``restrict_to_coarse`` takes that projection to be the
+same 4-point-per-direction Hermite stencil with the roles swapped (nodes at
+the fine cell centres, queries at the coarse cell centres), applied to C and
+to the fine surface-tension force, from which the coarse density and
+viscosity follow (Eqs. eq-rho, eq-mu, eq-fst).
+
 Readings (listed in the design doc): the cubic Hermite segment on [x_j, x_{j+1}]
 takes node slopes from central differences over the neighbouring nodes
 (non-uniform Catmull-Rom); the base node is the last node at or left of the
@@ -203,3 +210,27 @@ def fine_divergence(u, v, w, h, fine_n):
     dv = np.roll(v, -1, axis=1)[:, :ny, :] - v[:, :ny, :] if v.shape[1] == ny else v[:, 1:, :] - v[:, :-1, :]
     dw = np.roll(w, -1, axis=0)[:nz] - w[:nz] if w.shape[0] == nz else w[1:] - w[:-1]
     return (du + dv + dw) / h
+
+
+def restriction_tables(xf, yf, zf, fine_n, h, bc):
+    """Index maps and weights from fine cell centres to coarse cell centres."""
+    out = []
+    for d, faces in enumerate((xf, yf, zf)):
+        faces = np.asarray(faces, dtype=np.float64)
+        nodes = (np.arange(fine_n[d]) + 0.5) * h
+        out.append(weight_table(nodes, centres(faces), bc[d], fine_n[d] * h))
+    return out
+
+
+def restrict_to_coarse(C, p, xf, yf, zf, lam_rho, lam_mu):
+    """Down-sampling of Sec. 3.4: C and the fine surface-tension force F_st
+    (Eq. eq-fst) interpolated to the coarse cell centres by the 64-point
+    Hermite stencil, then rho and mu from the coarse C (Eqs. eq-rho, eq-mu).
+    ``p`` is the fine-mesh ch_oracle.Params.  Returns (C_c, rho_c, mu_c,
+    (Fx_c, Fy_c, Fz_c)), each [ncz][ncy][ncx]."""
+    from oracle import ch_oracle as co
+    tabs = restriction_tables(xf, yf, zf, (p.nx, p.ny, p.nz), p.h, p.bc)
+    Cc = interp_3d(np.asarray(C, dtype=np.float64), tabs)
+    F = co.surface_tension(np.asarray(C, dtype=np.float64), p)
+    Fc = tuple(interp_3d(f, tabs) for f in F)
+    return Cc, co.density(Cc, lam_rho), co.viscosity(Cc, lam_mu), Fc
