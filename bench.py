@@ -249,7 +249,8 @@ def multires_leg(args, dev, flush):
     """Multiple-resolution workload: seeded divergence-free coarse velocity on
     a 256 x 256 x 128 mesh (tanh-stretched z, walls at z = 0, 1) transferred
     to the 1024 x 1024 x 512 uniform FP32 fine mesh holding ~1000 drops of
-    radius U[0.01, 0.03]; times the transfer and the fine CH step."""
+    radius U[0.01, 0.03]; times the transfer, the down-sampling of C (with
+    rho, mu, F_st on the coarse mesh) and the fine CH step."""
     import torch
     from paper_2105_01865_gb300 import inputs, stability
     from paper_2105_01865_gb300.solver import Solver
@@ -283,6 +284,9 @@ def multires_leg(args, dev, flush):
 
     s.interp_to_fine()
     interp_ms = timed(s.interp_to_fine, 3)
+    # down-sampling back-coupling: coarse C, rho, mu and F_st (Sec. 3.4)
+    s.restrict_to_coarse(0.05, 1.0)
+    restrict_ms = timed(lambda: s.restrict_to_coarse(0.05, 1.0), 3)
     for _ in range(3):
         s.step(1)
     k = max(3, min(args.steps, 20))
@@ -291,7 +295,9 @@ def multires_leg(args, dev, flush):
     cells = nx * ny * nz
     out = dict(value=cells / (step_ms * 1e-3), unit="cell-updates/s", step_ms=step_ms, interp_ms=interp_ms,
                cells=cells, coarse_cells=256 * 256 * 128, drops=len(radii), steps=k, dtype="f32",
-               interp_fine_faces_gbs=3 * cells * 4 / (interp_ms * 1e-3) / 1e9)
+               interp_fine_faces_gbs=3 * cells * 4 / (interp_ms * 1e-3) / 1e9,
+               restrict_ms=restrict_ms,
+               restrict_fine_read_gbs=cells * 4 / (restrict_ms * 1e-3) / 1e9)
     s.close()
     return out
 

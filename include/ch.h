@@ -143,6 +143,27 @@ int ch_get_velocity_fine(ch_handle* h, void* u, void* v, void* w);
  * periodic directions) and weights[n_fine_dir][4] (double).  Synchronous. */
 int ch_get_interp_tables(ch_handle* h, int dir, int32_t* start, double* weights);
 
+/* Bytes of device workspace ch_restrict_to_coarse needs for this handle (0
+ * without a coarse mesh): 4 nz ny ncx + 4 nz ncy ncx elements of the
+ * handle's precision for the two intermediate passes. */
+size_t ch_restrict_workspace_bytes(const ch_handle* h);
+
+/* Down-sampling back-coupling (Sec. 3.4: the fine C projected directly to the
+ * stretched mesh, used for the coarse density, viscosity and surface tension;
+ * Sec. 2.2, Eqs. eq-rho, eq-mu, eq-fst).  The projection is the 4-point-per-
+ * direction Hermite stencil of the transfer with nodes at the fine cell
+ * centres and queries at the coarse cell centres, applied to C and to the
+ * fine F_st = 6 sqrt(2) phi grad C / Cn (phi = psi'(C) - Cn^2 lap_h C, central
+ * differences, the step's ghost cells).  Outputs (DEVICE, caller-owned,
+ * [ncz][ncy][ncx], the handle's precision): C_c, rho_c = C_c + lambda_rho
+ * (1 - C_c), mu_c = C_c + lambda_mu (1 - C_c), and the three F_st components
+ * at the coarse cell centres.  work: >= ch_restrict_workspace_bytes(h) bytes,
+ * 256-byte aligned.  Requires a coarse mesh.  Asynchronous.  Errors:
+ * CH_EINVAL (no coarse mesh, NULL/misaligned pointers, non-finite ratios),
+ * CH_ENOMEM (workspace too small), CH_ECUDA. */
+int ch_restrict_to_coarse(ch_handle* h, double lambda_rho, double lambda_mu, void* C_c, void* rho_c, void* mu_c,
+                          void* fx_c, void* fy_c, void* fz_c, void* work, size_t work_bytes);
+
 /* Advance C by nsteps full RK3 steps (three substeps each; Sec. 3 and
  * Eqs. eq-re .. eq-fac-3).  Asynchronous; a non-finite C sets a device flag
  * reported by the next ch_sync / ch_mass / ch_free_energy.  nsteps >= 0. */

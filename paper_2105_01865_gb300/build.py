@@ -11,7 +11,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libch.so")
-SOURCES = ["ch_step.cu", "ch_mr.cu", "ch_noalloc.cu", "ch_batch.cu", "ch_adjoint.cu", "ch_standard.cu"]
+SOURCES = ["ch_step.cu", "ch_mr.cu", "ch_noalloc.cu", "ch_batch.cu", "ch_adjoint.cu", "ch_standard.cu", "ch_restrict.cu"]
 HEADERS = ["ch_internal.h", "ch_kernels.cuh", "ch_explicit2.cuh", "ch_cols2.cuh", "line_tables.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]

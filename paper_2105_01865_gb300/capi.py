@@ -57,6 +57,9 @@ SIGNATURES = [
     ("ch_interp_to_fine", ctypes.c_int, [_P]),
     ("ch_get_velocity_fine", ctypes.c_int, [_P, _P, _P, _P]),
     ("ch_get_interp_tables", ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    ("ch_restrict_workspace_bytes", ctypes.c_size_t, [_P]),
+    ("ch_restrict_to_coarse", ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, _P, _P, _P, _P, _P, _P, _P,
+                                             ctypes.c_size_t]),
     ("ch_step", ctypes.c_int, [_P, ctypes.c_int64]),
     ("ch_mass", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     ("ch_free_energy", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
@@ -177,6 +180,16 @@ def ch_get_interp_tables(handle, direction, n):
     _check(load().ch_get_interp_tables(handle, direction, start.ctypes.data_as(ctypes.c_void_p),
                                        wts.ctypes.data_as(ctypes.c_void_p)), handle, "ch_get_interp_tables")
     return start, wts
+
+
+def ch_restrict_workspace_bytes(handle):
+    return int(load().ch_restrict_workspace_bytes(handle))
+
+
+def ch_restrict_to_coarse(handle, lam_rho, lam_mu, outs, work):
+    """outs: six device tensors (C_c, rho_c, mu_c, Fx_c, Fy_c, Fz_c); work: a uint8 device tensor."""
+    _check(load().ch_restrict_to_coarse(handle, lam_rho, lam_mu, *[_ptr(t) for t in outs], _ptr(work),
+                                        work.numel()), handle, "ch_restrict_to_coarse")
 
 
 def ch_step(handle, nsteps):

@@ -61,6 +61,11 @@ struct ch_handle {
     int32_t* mr_start[3];
     double* mr_w[3];
     double* mr_coords;  // device copy of coarse face coordinates (x, y, z concatenated)
+    // down-sampling tables: per coarse cell index, the first of 4 fine nodes and
+    // the weights (doubles [nc][4] then floats [nc][4])
+    int32_t* rs_start[3];
+    double* rs_w[3];
+    double* rs_coords;  // fine faces (x, y, z) then coarse centres (x, y, z)
     // CUDA graph of one full step
     cudaGraphExec_t graph;
     int graph_ready;
@@ -100,5 +105,9 @@ int launch_substep_standard(ch_handle* h, int l, cudaEvent_t* ev);
 // multi-resolution entry points implemented in ch_mr.cu
 int mr_build_tables(ch_handle* h, const double* xf, const double* yf, const double* zf);
 void mr_destroy(ch_handle* h);
+int mr_tables_launch(ch_handle* h, const double* faces, int nc, int periodic, int nq, const double* queries,
+                     int32_t* start, double* w);
+// down-sampling tables (ch_restrict.cu), built by ch_create after mr_build_tables
+int rs_build_tables(ch_handle* h, const double* xf, const double* yf, const double* zf);
 
 }  // namespace chg

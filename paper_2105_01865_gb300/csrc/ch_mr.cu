@@ -25,11 +25,12 @@ constexpr int kThreads = 256;
 // stencil is clamped into the node range); periodic directions wrap.
 // ---------------------------------------------------------------------------
 __global__ void mr_tables_kernel(const double* __restrict__ faces, int nc, int periodic, int nfine, double h,
-                                 int32_t* __restrict__ start_out, double* __restrict__ w_out,
-                                 float* __restrict__ wf_out) {
+                                 const double* __restrict__ queries, int32_t* __restrict__ start_out,
+                                 double* __restrict__ w_out, float* __restrict__ wf_out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nfine) return;
-    const double x = ((double)i + 0.5) * h;
+    // query point: the fine cell centre, or an explicit coordinate (restriction tables)
+    const double x = queries ? queries[i] : ((double)i + 0.5) * h;
     const double P = faces[nc] - faces[0];
     auto node = [&](int k) { return 0.5 * (faces[k] + faces[k + 1]); };
     // j = max{j : node_j <= x}, -1 if none (binary search)
@@ -418,10 +419,24 @@ namespace chg {
 
 void mr_destroy(ch_handle* h) {
     cudaFree(h->mr_coords);
+    cudaFree(h->rs_coords);
     for (int d = 0; d < 3; ++d) {
         cudaFree(h->mr_start[d]);
         cudaFree(h->mr_w[d]);
+        cudaFree(h->rs_start[d]);
+        cudaFree(h->rs_w[d]);
     }
+}
+
+// Hermite tables of nq query points against the nodes at the centres of the
+// nc cells bounded by faces (device arrays); weights as doubles [nq][4] then
+// floats [nq][4] in w.
+int mr_tables_launch(ch_handle* h, const double* faces, int nc, int periodic, int nq, const double* queries,
+                     int32_t* start, double* w) {
+    mr_tables_kernel<<<(unsigned)((nq + kThreads - 1) / kThreads), kThreads, 0, h->stream>>>(
+        faces, nc, periodic, nq, h->p.h, queries, start, w, (float*)(w + 4 * (int64_t)nq));
+    CHG_CUDA(h, cudaGetLastError());
+    return CH_OK;
 }
 
 // Called from ch_create with the caller's host face coordinates.
@@ -442,7 +457,7 @@ int mr_build_tables(ch_handle* h, const double* xf, const double* yf, const doub
         // doubles [n][4] followed by floats [n][4]
         if (cudaMalloc(&h->mr_w[d], n * 4 * sizeof(double) + n * 4 * sizeof(float)) != cudaSuccess) return CH_ENOMEM;
         mr_tables_kernel<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, h->stream>>>(
-            dev_faces[d], (int)h->nc[d], h->p.bc[d] == CH_PERIODIC, (int)n, h->p.h, h->mr_start[d], h->mr_w[d],
+            dev_faces[d], (int)h->nc[d], h->p.bc[d] == CH_PERIODIC, (int)n, h->p.h, nullptr, h->mr_start[d], h->mr_w[d],
             (float*)(h->mr_w[d] + 4 * n));
         CHG_CUDA(h, cudaGetLastError());
     }

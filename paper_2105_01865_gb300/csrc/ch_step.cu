@@ -633,6 +633,7 @@ int ch_create(const ch_params* p, void* C, void* work, size_t work_bytes, void* 
     }
     if (rc == CH_OK) rc = h->prec == CH_F64 ? set_smem_attrs<double>(h) : set_smem_attrs<float>(h);
     if (rc == CH_OK && p->ncx) rc = mr_build_tables(h, p->xf_coarse, p->yf_coarse, p->zf_coarse);
+    if (rc == CH_OK && p->ncx) rc = rs_build_tables(h, p->xf_coarse, p->yf_coarse, p->zf_coarse);
     if (rc != CH_OK) {
         ch_free(h);
         return rc;

@@ -81,6 +81,24 @@ class Solver:
         self.stream.synchronize()
         return out
 
+    def restrict_to_coarse(self, lam_rho, lam_mu):
+        """Down-sampling of C (Sec. 3.4) and the coarse rho, mu and surface
+        tension (Eqs. eq-rho, eq-mu, eq-fst).  Returns a dict of device
+        tensors [ncz][ncy][ncx]: C, rho, mu, Fx, Fy, Fz (asynchronous on the
+        solver's stream)."""
+        if not hasattr(self, "coarse_shapes"):
+            raise ValueError("restrict_to_coarse needs a coarse mesh")
+        ncz, ncy = self.coarse_shapes[0][0], self.coarse_shapes[0][1]
+        ncx = self.coarse_shapes[1][2]
+        names = ("C", "rho", "mu", "Fx", "Fy", "Fz")
+        outs = [torch.empty((ncz, ncy, ncx), dtype=self.dtype, device=self.device) for _ in names]
+        if getattr(self, "_rs_work", None) is None:
+            self._rs_work = torch.empty(capi.ch_restrict_workspace_bytes(self.handle), dtype=torch.uint8,
+                                        device=self.device)
+        self._order()
+        capi.ch_restrict_to_coarse(self.handle, lam_rho, lam_mu, outs, self._rs_work)
+        return dict(zip(names, outs))
+
     def interp_tables(self, direction):
         n = (self.shape[2], self.shape[1], self.shape[0])[direction]
         return capi.ch_get_interp_tables(self.handle, direction, n)
