@@ -207,9 +207,15 @@ __device__ __forceinline__ void solve_cols2_tile(T* a, T* Cf, int nx, int64_t ou
     if (UPDATE && bad) atomicOr(status, 1u);
 }
 
-// Up to 128 registers a thread: a lane holds R row pairs.
+// Up to 128 registers a thread (a lane holds R row pairs); shapes of 16 or
+// more warps with 8 rows target 64 registers, for twice the resident warps.
+template <int R, int NW>
+struct Cols2MinBlocks {
+    static constexpr int kThreadsPerSm = (R <= 8 && NW >= 16) ? 1024 : 512;
+    static constexpr int value = kThreadsPerSm / (NW * 32) > 0 ? kThreadsPerSm / (NW * 32) : 1;
+};
 template <typename T, int R, int NW, bool UPDATE>
-__global__ void __launch_bounds__(NW * 32, (512 / (NW * 32)) > 0 ? 512 / (NW * 32) : 1)
+__global__ void __launch_bounds__(NW * 32, Cols2MinBlocks<R, NW>::value)
 ch_solve_cols2(T* __restrict__ a, T* __restrict__ Cf, int nx, int64_t outer_stride, int64_t line_stride,
                CCoef<T> cf, unsigned int* status) {
     extern __shared__ __align__(16) unsigned char cols2_raw[];

@@ -264,6 +264,8 @@ int set_attrs_cols2_all(ch_handle* h) {
     if (rc == CH_OK) rc = set_attrs_cols2<T, 8, 8>(h);
     if (rc == CH_OK) rc = set_attrs_cols2<T, 16, 8>(h);
     if (rc == CH_OK) rc = set_attrs_cols2<T, 16, 16>(h);
+    if (rc == CH_OK) rc = set_attrs_cols2<T, 8, 16>(h);
+    if (rc == CH_OK) rc = set_attrs_cols2<T, 8, 32>(h);
     return rc;
 }
 
@@ -297,6 +299,8 @@ int launch_cols(ch_handle* h, int l, int dir, T* r, T* Cupd) {
                 }
             }
             if (lt.nw == 16 && lt.R == 16) return launch_cols2_rn<T, 16, 16>(h, l, dir, r, Cupd);
+            if (lt.nw == 16 && lt.R == 8) return launch_cols2_rn<T, 8, 16>(h, l, dir, r, Cupd);
+            if (lt.nw == 32 && lt.R == 8) return launch_cols2_rn<T, 8, 32>(h, l, dir, r, Cupd);
             // 32 warps leave 64 registers a thread: the one-column form below
         }
     }
@@ -312,6 +316,8 @@ int launch_cols(ch_handle* h, int l, int dir, T* r, T* Cupd) {
     }
     if (lt.nw == 16 && lt.R == 16) return launch_cols_rn<T, 16, 16>(h, l, dir, r, Cupd);
     if (lt.nw == 32 && lt.R == 16) return launch_cols_rn<T, 16, 32>(h, l, dir, r, Cupd);
+    if (lt.nw == 16 && lt.R == 8) return launch_cols_rn<T, 8, 16>(h, l, dir, r, Cupd);
+    if (lt.nw == 32 && lt.R == 8) return launch_cols_rn<T, 8, 32>(h, l, dir, r, Cupd);
     return -1;
 }
 

@@ -381,18 +381,25 @@ inline std::vector<double> col_tables(const LineFactors& F, int nw, int R) {
 // Column-solver shape for a line of n cells: nw warps of R rows (powers of
 // two; R <= 16 keeps a warp's rows in registers at full occupancy).  Returns
 // false for lines longer than 512.
+#ifndef CH_COLUMN_MAXR
+#define CH_COLUMN_MAXR 16
+#endif
 inline bool col_shape(int n, int* nw, int* R) {
     if (n <= 128) {
         int r = 1;
         while (8 * r < n) r *= 2;
         *nw = 8;
         *R = r;
+        if (r > CH_COLUMN_MAXR) {  // more warps of fewer register rows
+            *R = CH_COLUMN_MAXR;
+            *nw = 128 / CH_COLUMN_MAXR;
+        }
         return true;
     }
     if (n <= 256) {
-        *nw = 16;
-        *R = 16;
-        return true;
+        *R = CH_COLUMN_MAXR;
+        *nw = 256 / CH_COLUMN_MAXR;
+        return *nw <= 32;
     }
     if (n <= 512) {
         *nw = 32;
