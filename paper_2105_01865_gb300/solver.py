@@ -84,8 +84,9 @@ class Solver:
     def restrict_to_coarse(self, lam_rho, lam_mu):
         """Down-sampling of C (Sec. 3.4) and the coarse rho, mu and surface
         tension (Eqs. eq-rho, eq-mu, eq-fst).  Returns a dict of device
-        tensors [ncz][ncy][ncx]: C, rho, mu, Fx, Fy, Fz (asynchronous on the
-        solver's stream)."""
+        tensors [ncz][ncy][ncx]: C, rho, mu, Fx, Fy, Fz.  Asynchronous: the
+        work runs on the solver's stream and torch's current stream is made
+        to wait for it."""
         if not hasattr(self, "coarse_shapes"):
             raise ValueError("restrict_to_coarse needs a coarse mesh")
         ncz, ncy = self.coarse_shapes[0][0], self.coarse_shapes[0][1]
@@ -97,6 +98,8 @@ class Solver:
                                         device=self.device)
         self._order()
         capi.ch_restrict_to_coarse(self.handle, lam_rho, lam_mu, outs, self._rs_work)
+        # torch work on the returned tensors (on the current stream) waits for the library's
+        torch.cuda.current_stream(self.device).wait_stream(self.stream)
         return dict(zip(names, outs))
 
     def interp_tables(self, direction):

@@ -105,3 +105,18 @@ def test_launch_count_and_adjoint_refused():
     assert s.launches_per_step() == 6
     with pytest.raises(capi.CHError):
         s.adjoint(C0, 2, np.ones(shape), 1)
+
+
+def test_full_size_shear_drop_one_step():
+    """The bench's comparison box (256 x 256 x 128 shear drop, FP32) at the
+    standard scheme's stable dt: one step against the oracle."""
+    f = inputs.shear_drop_box(256, 256, 128)
+    h = f["h"]
+    dt = min(0.9 * stability.stable_dt_standard(f["shape"], h, f["bc"], f["cn"], f["pe"]), 0.5 * h / 0.5)
+    s = make(f["shape"], h, f["bc"], f["cn"], f["pe"], dt, f["C"], "f32", f["vel"])
+    s.step(1)
+    ref = co.step_standard(f["C"].astype(np.float32).astype(np.float64), f["vel"],
+                           params(f["shape"], h, f["bc"], f["cn"], f["pe"], dt), 1)
+    err = rel_l2(s.field(), ref)
+    print(f"FP32 standard scheme 256x256x128, 1 step: rel L2 on C = {err:.3e}")
+    assert err <= 1e-6
