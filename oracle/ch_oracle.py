@@ -41,6 +41,7 @@ import scipy.linalg
 
 PERIODIC = 0
 NOFLUX = 1
+DIRICHLET = 2   # C = 0 on the wall faces (the Rayleigh-Benard walls of Sec. 4.3); walls for the flow
 
 # Low-storage RK3 of Sec. 3 (coefficients not printed in the paper; the
 # published three-substep scheme of the cited RK reference).
@@ -87,7 +88,7 @@ class Params:
 
     def nfaces(self, d):
         """Number of face-velocity planes normal to direction d (staggered mesh)."""
-        return self.n(d) + (1 if self.bc[d] == NOFLUX else 0)
+        return self.n(d) + (1 if self.bc[d] != PERIODIC else 0)
 
 
 # ---------------------------------------------------------------------------
@@ -113,11 +114,22 @@ def _axis(d):
 
 
 def pad(f, bc, g):
-    """Add g ghost layers per side: wrap (periodic) or mirror about the wall face."""
+    """Add g ghost layers per side: wrap (periodic), mirror about the wall face
+    (no-flux), or mirror with the sign flipped (Dirichlet C = 0 on the wall
+    face: the ghost C_{-1-m} = -C_m)."""
     for d in range(3):
         width = [(0, 0)] * 3
-        width[_axis(d)] = (g, g)
+        a = _axis(d)
+        width[a] = (g, g)
         f = np.pad(f, width, mode="wrap" if bc[d] == PERIODIC else "symmetric")
+        if bc[d] == DIRICHLET:
+            f = f.copy()
+            lo = [slice(None)] * 3
+            lo[a] = slice(0, g)
+            hi = [slice(None)] * 3
+            hi[a] = slice(f.shape[a] - g, f.shape[a])
+            f[tuple(lo)] *= -1.0
+            f[tuple(hi)] *= -1.0
     return f
 
 
@@ -182,7 +194,7 @@ def face_fluxes(C, vel, p: Params, d):
     vlow = np.take(vel, np.arange(n), axis=a)          # velocity at face f = lower face of cell f
     Cf = np.where(vlow >= 0.0, left, right)
     F = vlow * Cf
-    if p.bc[d] == NOFLUX:
+    if p.bc[d] != PERIODIC:
         F = F.copy()
         idx = [slice(None)] * 3
         idx[a] = 0
@@ -213,20 +225,24 @@ def line_operator(n, bc, kappa):
     """Dense n x n matrix of the 1D pentadiagonal operator A_d of Eq. (eq-a3d).
 
     Each row applies kappa*[1, -4, 6, -4, 1]; neighbours beyond the boundary
-    are the wrapped (periodic) or mirrored (no-flux wall) cells, which fixes
-    the 'first and last rows determined by boundary conditions' of Eq. (eq-a2d).
+    are the wrapped (periodic) or mirrored (no-flux wall) cells, the mirrored
+    ones with a sign flip for a Dirichlet wall, which fixes the 'first and last
+    rows determined by boundary conditions' of Eq. (eq-a2d).
     """
     A = np.zeros((n, n))
     for i in range(n):
         for s, c in zip((-2, -1, 0, 1, 2), (1.0, -4.0, 6.0, -4.0, 1.0)):
             j = i + s
+            sign = 1.0
             if bc == PERIODIC:
                 j %= n
             elif j < 0:
                 j = -1 - j
+                sign = -1.0 if bc == DIRICHLET else 1.0
             elif j >= n:
                 j = 2 * n - 1 - j
-            A[i, j] += kappa * c
+                sign = -1.0 if bc == DIRICHLET else 1.0
+            A[i, j] += sign * kappa * c
     return A
 
 

@@ -194,12 +194,12 @@ def transfer(uc, vc, wc, xf, yf, zf, fine_n, h, bc):
         return np.expand_dims(ref, axis) + run
 
     # reference planes: u at x-face 0 interpolated in (z, y); v at y-face 0 in (z, x); w at z-face 0 in (y, x)
-    u_ref = np.zeros((nz, ny)) if bc[0] == NOFLUX else interp_plane(uc[:, :, 0], tz, ty)
-    v_ref = np.zeros((nz, nx)) if bc[1] == NOFLUX else interp_plane(vc[:, 0, :], tz, tx)
-    w_ref = np.zeros((ny, nx)) if bc[2] == NOFLUX else interp_plane(wc[0, :, :], ty, tx)
-    u = integrate(Gx, u_ref, 2, bc[0] == NOFLUX)
-    v = integrate(Gy, v_ref, 1, bc[1] == NOFLUX)
-    w = integrate(Gz, w_ref, 0, bc[2] == NOFLUX)
+    u_ref = np.zeros((nz, ny)) if bc[0] != PERIODIC else interp_plane(uc[:, :, 0], tz, ty)
+    v_ref = np.zeros((nz, nx)) if bc[1] != PERIODIC else interp_plane(vc[:, 0, :], tz, tx)
+    w_ref = np.zeros((ny, nx)) if bc[2] != PERIODIC else interp_plane(wc[0, :, :], ty, tx)
+    u = integrate(Gx, u_ref, 2, bc[0] != PERIODIC)
+    v = integrate(Gy, v_ref, 1, bc[1] != PERIODIC)
+    w = integrate(Gz, w_ref, 0, bc[2] != PERIODIC)
     return (u, v, w), tabs
 
 
