@@ -56,6 +56,7 @@ extern "C" {
  * determined by boundary conditions") */
 #define CH_PERIODIC 0    /* wrap: cyclic pentadiagonal line solves */
 #define CH_NOFLUX 1      /* walls: mirror ghosts C_{-1-m} = C_m, zero wall flux */
+#define CH_DIRICHLET 2   /* z only: C = 0 on the wall faces (antisymmetric ghosts); a wall for the flow */
 
 /* arithmetic precision of fields and kernels */
 #define CH_F32 0         /* float fields, float arithmetic; FP64 reductions */
@@ -68,7 +69,7 @@ extern "C" {
 typedef struct ch_params {
     int64_t nx, ny, nz;   /* fine cells per direction, each >= 5 */
     double h;             /* uniform fine spacing (Sec. 3: same h in all directions) */
-    int32_t bc[3];        /* CH_PERIODIC / CH_NOFLUX for x, y, z */
+    int32_t bc[3];        /* CH_PERIODIC / CH_NOFLUX for x, y, z; z may also be CH_DIRICHLET */
     int32_t precision;    /* CH_F32 or CH_F64 */
     double cn;            /* Cahn number Cn (> 0) */
     double pe;            /* Peclet number Pe (> 0); mobility M = 1/Pe */

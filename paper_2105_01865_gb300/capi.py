@@ -17,7 +17,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libch.so")
 
 CH_OK, CH_EINVAL, CH_ECUDA, CH_ENONFINITE, CH_ETIMEOUT, CH_ENOMEM = range(6)
-CH_PERIODIC, CH_NOFLUX = 0, 1
+CH_PERIODIC, CH_NOFLUX, CH_DIRICHLET = 0, 1, 2
 CH_F32, CH_F64 = 0, 1
 CH_SCHEME_SPLIT, CH_SCHEME_STANDARD = 0, 1
 

@@ -142,6 +142,7 @@ int ch_step_adjoint(ch_handle* h, const void* C0, int64_t nsteps, int64_t ckpt_e
     if (h->p.advect) return fail(h, CH_EINVAL, "ch_step_adjoint: only u = 0 (advect = 0) is supported");
     if (h->p.scheme != CH_SCHEME_SPLIT) return fail(h, CH_EINVAL, "ch_step_adjoint: only the split scheme");
     if (h->n[2] < 5) return fail(h, CH_EINVAL, "ch_step_adjoint: needs nz >= 5");
+    if (h->p.bc[2] == CH_DIRICHLET) return fail(h, CH_EINVAL, "ch_step_adjoint: Dirichlet walls are not supported");
     if (!C0 || !lam_T || !lam_0 || !dL_dM || !work || nsteps < 1 || ckpt_every < 1 || ((uintptr_t)work % 256))
         return fail(h, CH_EINVAL, "ch_step_adjoint: bad argument");
     const AdjLayout L = adj_layout(h, nsteps, ckpt_every);

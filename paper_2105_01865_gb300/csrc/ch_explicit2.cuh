@@ -211,13 +211,17 @@ __device__ __forceinline__ void explicit_tile2(const T* C, const T* u, const T* 
     // z-column queue of pairs: q[m] = C(ia..ia+1, jc, k - 2 + m)
     Pr<T> q[6];
 #pragma unroll
-    for (int m = 0; m < 6; ++m) q[m] = ldp(C + (bc_near(k0 - 2 + m, a.nz, a.bcz) * plane + col));
+    for (int m = 0; m < 6; ++m) {
+        q[m] = ldp(C + (bc_near(k0 - 2 + m, a.nz, a.bcz) * plane + col));
+        if (bc_negate(k0 - 2 + m, a.nz, a.bcz)) q[m] = sub(sp<T>(T(0)), q[m]);
+    }
 
     Pr<T> fz_lo = sp<T>(T(0));
     if (ADV) {
-        const bool wall = (a.bcz == CH_NOFLUX) && (k0 == 0);
+        const bool wall = (a.bcz != CH_PERIODIC) && (k0 == 0);
         if (!wall) {
-            const Pr<T> cm3 = ldp(C + (bc_near(k0 - 3, a.nz, a.bcz) * plane + col));
+            Pr<T> cm3 = ldp(C + (bc_near(k0 - 3, a.nz, a.bcz) * plane + col));
+            if (bc_negate(k0 - 3, a.nz, a.bcz)) cm3 = sub(sp<T>(T(0)), cm3);
             const Pr<T> wv = ldp(w + (k0 * plane + col));
             fz_lo = face_flux_p(wv, cm3, q[0], q[1], q[2], q[3], q[4], eps);
         }
@@ -264,11 +268,12 @@ __device__ __forceinline__ void explicit_tile2(const T* C, const T* u, const T* 
             cp_async_wait<0>();
         }
         // per-thread global inputs of this plane (issued before the barrier)
-        const Pr<T> qnext = ldp(C + (bc_near(k + 4, a.nz, a.bcz) * plane + col));
+        Pr<T> qnext = ldp(C + (bc_near(k + 4, a.nz, a.bcz) * plane + col));
+        if (bc_negate(k + 4, a.nz, a.bcz)) qnext = sub(sp<T>(T(0)), qnext);
         const int kp = k * a.ny;
         T uxa = T(0), uxb = T(0), uxe_a = T(0), uxe_b = T(0);
         Pr<T> vy = sp<T>(T(0)), vye = sp<T>(T(0)), wz = sp<T>(T(0)), hp = sp<T>(T(0));
-        const bool zwall = (a.bcz == CH_NOFLUX) && (k + 1 >= a.nz);
+        const bool zwall = (a.bcz != CH_PERIODIC) && (k + 1 >= a.nz);
         if (ADV) {
             uxa = wxa ? T(0) : u[(kp + jc) * a.nfx + fxa];
             uxb = wxb ? T(0) : u[(kp + jc) * a.nfx + fxb];
@@ -333,9 +338,14 @@ __device__ __forceinline__ void explicit_tile2(const T* C, const T* u, const T* 
         // formed first, so FP32 keeps the accuracy of the small differences
         const Pr<T> xl = mk(s3, s4), xr = mk(s5, s6);
         const Pr<T> pc = psi_pp(c0);
+        Pr<T> pzm = psi_pp(q[1]), pzp = psi_pp(q[3]);
+        if (a.bcz == CH_DIRICHLET) {  // the ghost of psi' is its own negated mirror (psi' = 0 on the wall)
+            if (k == 0) pzm = sub(sp<T>(T(0)), psi_pp(sub(sp<T>(T(0)), q[1])));
+            if (k + 1 == a.nz) pzp = sub(sp<T>(T(0)), psi_pp(sub(sp<T>(T(0)), q[3])));
+        }
         const Pr<T> lap = mul(add(add(add(sub(psi_pp(xl), pc), sub(psi_pp(xr), pc)),
                                       add(sub(psi_pp(ym1), pc), sub(psi_pp(yp1), pc))),
-                                  add(sub(psi_pp(q[1]), pc), sub(psi_pp(q[3]), pc))),
+                                  add(sub(pzm, pc), sub(pzp, pc))),
                               sp<T>(a.inv_h2));
         // [1,-4,6,-4,1] sums of A_x + A_y + A_z (Eq. eq-a3d) as differences of
         // second differences: D2(i-1) - 2 D2(i) + D2(i+1)

@@ -57,6 +57,10 @@ __device__ __forceinline__ int bc_index(int i, int n, int bc) {
 
 // The same rule for indices at most one period outside [0, n) (n >= 5 and
 // offsets of at most 4), without division.
+// Sign of the ghost value at index i: -1 beyond a Dirichlet wall (C = 0 on
+// the wall face, so the ghost is the negated mirror), else +1.
+__device__ __forceinline__ bool bc_negate(int i, int n, int bc) { return bc == CH_DIRICHLET && (i < 0 || i >= n); }
+
 __device__ __forceinline__ int bc_near(int i, int n, int bc) {
     if (n == 1) return 0;  // a single periodic plane: every neighbour is the plane itself
     if (i < 0) return bc == CH_PERIODIC ? i + n : -1 - i;
@@ -176,14 +180,18 @@ ch_explicit_rhs(const T* __restrict__ C, const T* __restrict__ u, const T* __res
     // z-column queue: q[m] = C(ic, jc, k - 2 + m), m = 0..5
     T q[6];
 #pragma unroll
-    for (int m = 0; m < 6; ++m) q[m] = C[(int64_t)bc_near(k0 - 2 + m, a.nz, a.bcz) * plane + col];
+    for (int m = 0; m < 6; ++m) {
+        q[m] = C[(int64_t)bc_near(k0 - 2 + m, a.nz, a.bcz) * plane + col];
+        if (bc_negate(k0 - 2 + m, a.nz, a.bcz)) q[m] = -q[m];
+    }
 
     T fz_lo = T(0);
     if (ADV) {
         // flux through the lower z-face of plane k0
-        const bool wall = (a.bcz == CH_NOFLUX) && (k0 == 0);
+        const bool wall = (a.bcz != CH_PERIODIC) && (k0 == 0);
         if (!wall) {
-            const T cm3 = C[(int64_t)bc_near(k0 - 3, a.nz, a.bcz) * plane + col];
+            T cm3 = C[(int64_t)bc_near(k0 - 3, a.nz, a.bcz) * plane + col];
+            if (bc_negate(k0 - 3, a.nz, a.bcz)) cm3 = -cm3;
             const T wv = w[(int64_t)k0 * plane + col];
             fz_lo = face_flux(wv, cm3, q[0], q[1], q[2], q[3], q[4], eps);
         }
@@ -210,7 +218,8 @@ ch_explicit_rhs(const T* __restrict__ C, const T* __restrict__ u, const T* __res
             cp_async_wait<0>();
         }
         // prefetch the next queue entry C(k + 4)
-        const T qnext = C[(int64_t)bc_near(k + 4, a.nz, a.bcz) * plane + col];
+        T qnext = C[(int64_t)bc_near(k + 4, a.nz, a.bcz) * plane + col];
+        if (bc_negate(k + 4, a.nz, a.bcz)) qnext = -qnext;
         __syncthreads();
 
         const int cy = ty + kHalo, cx = tx + kHalo;
@@ -260,7 +269,7 @@ ch_explicit_rhs(const T* __restrict__ C, const T* __restrict__ u, const T* __res
             }
             // z: flux through the upper face k+1 of this cell
             {
-                const bool wall = (a.bcz == CH_NOFLUX) && (k + 1 >= a.nz);
+                const bool wall = (a.bcz != CH_PERIODIC) && (k + 1 >= a.nz);
                 if (!wall) {
                     const int f = (k + 1 < a.nz) ? k + 1 : 0;
                     const T wv = w[(int64_t)f * plane + col];
@@ -274,9 +283,14 @@ ch_explicit_rhs(const T* __restrict__ C, const T* __restrict__ u, const T* __res
         // formed first, so FP32 keeps the accuracy of the small differences
         const T c0 = Cs[buf][cy][cx];
         const T pc = psi_p(c0);
+        T pzm = psi_p(q[1]), pzp = psi_p(q[3]);
+        if (a.bcz == CH_DIRICHLET) {  // the ghost of psi' is its own negated mirror (psi' = 0 on the wall)
+            if (k == 0) pzm = -psi_p(-q[1]);
+            if (k + 1 == a.nz) pzp = -psi_p(-q[3]);
+        }
         const T lap = (((psi_p(Cs[buf][cy][cx - 1]) - pc) + (psi_p(Cs[buf][cy][cx + 1]) - pc)) +
                        ((psi_p(Cs[buf][cy - 1][cx]) - pc) + (psi_p(Cs[buf][cy + 1][cx]) - pc)) +
-                       ((psi_p(q[1]) - pc) + (psi_p(q[3]) - pc))) *
+                       ((pzm - pc) + (pzp - pc))) *
                       a.inv_h2;
         // [1,-4,6,-4,1] sums of A_x + A_y + A_z (Eq. eq-a3d) as differences of
         // second differences: D2(i-1) - 2 D2(i) + D2(i+1)
@@ -964,9 +978,10 @@ ch_reduce_energy(const T* __restrict__ C, int nx, int ny, int nz, int bcx, int b
         const int ip = (i + 1 < nx) ? i + 1 : (bcx == CH_PERIODIC ? 0 : i);
         const int jp = (j + 1 < ny) ? j + 1 : (bcy == CH_PERIODIC ? 0 : j);
         const int kp = (k + 1 < nz) ? k + 1 : (bcz == CH_PERIODIC ? 0 : k);
+        const double zsign = (k + 1 >= nz && bcz == CH_DIRICHLET) ? -1.0 : 1.0;  // ghost -C at a Dirichlet wall
         const double gx = ((double)C[e - i + ip] - c) * inv_h;
         const double gy = ((double)C[e + (int64_t)(jp - j) * nx] - c) * inv_h;
-        const double gz = ((double)C[e + (int64_t)(kp - k) * nx * ny] - c) * inv_h;
+        const double gz = (zsign * (double)C[e + (int64_t)(kp - k) * nx * ny] - c) * inv_h;
         const double cc = c * (c - 1.0);
         acc += 0.25 * cc * cc + half_cn2 * (gx * gx + gy * gy + gz * gz);
     }

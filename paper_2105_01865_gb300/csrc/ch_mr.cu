@@ -358,7 +358,7 @@ MrArgs mr_args(const ch_handle* h) {
     a.ncfx = (int)h->ncf[0];
     a.ncfy = (int)h->ncf[1];
     a.ncfz = (int)h->ncf[2];
-    for (int d = 0; d < 3; ++d) a.wall[d] = h->p.bc[d] == CH_NOFLUX;
+    for (int d = 0; d < 3; ++d) a.wall[d] = h->p.bc[d] != CH_PERIODIC;
     a.h = h->p.h;
     return a;
 }

@@ -228,6 +228,8 @@ int ch_restrict_to_coarse(ch_handle* h, double lambda_rho, double lambda_mu, voi
                           void* fx_c, void* fy_c, void* fz_c, void* work, size_t work_bytes) {
     if (!h) return CH_EINVAL;
     if (!h->nc[0]) return fail(h, CH_EINVAL, "ch_restrict_to_coarse: the handle has no coarse mesh");
+    if (h->p.bc[2] == CH_DIRICHLET)
+        return fail(h, CH_EINVAL, "ch_restrict_to_coarse: Dirichlet walls are not supported");
     void* out[6] = {C_c, rho_c, mu_c, fx_c, fy_c, fz_c};
     for (void* o : out)
         if (!o || ((uintptr_t)o % h->esz)) return fail(h, CH_EINVAL, "ch_restrict_to_coarse: bad output pointer");

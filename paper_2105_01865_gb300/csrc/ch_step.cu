@@ -68,7 +68,10 @@ bool params_valid(const ch_params* p, char* why, size_t wl) {
         !std::isfinite(p->w) || !std::isfinite(p->weno_eps))
         return bad("non-finite parameter");
     for (int d = 0; d < 3; ++d)
-        if (p->bc[d] != CH_PERIODIC && p->bc[d] != CH_NOFLUX) return bad("bc must be CH_PERIODIC or CH_NOFLUX");
+        if (p->bc[d] != CH_PERIODIC && p->bc[d] != CH_NOFLUX && !(d == 2 && p->bc[d] == CH_DIRICHLET))
+            return bad("bc must be CH_PERIODIC or CH_NOFLUX (z may also be CH_DIRICHLET)");
+    if (p->bc[2] == CH_DIRICHLET && p->scheme != CH_SCHEME_SPLIT)
+        return bad("Dirichlet walls are supported by the split scheme only");
     if (p->precision != CH_F32 && p->precision != CH_F64) return bad("precision must be CH_F32 or CH_F64");
     if (p->advect != 0 && p->advect != 1) return bad("advect must be 0 or 1");
     if (p->scheme != CH_SCHEME_SPLIT && p->scheme != CH_SCHEME_STANDARD)
@@ -121,7 +124,7 @@ Layout layout(const ch_params* p) {
     L.r = take(N * esz);
     const int64_t n[3] = {p->nx, p->ny, p->nz};
     int64_t nf[3];
-    for (int d = 0; d < 3; ++d) nf[d] = n[d] + (p->bc[d] == CH_NOFLUX ? 1 : 0);
+    for (int d = 0; d < 3; ++d) nf[d] = n[d] + (p->bc[d] != CH_PERIODIC ? 1 : 0);
     if (p->advect) {
         L.vel[0] = take((size_t)n[2] * n[1] * nf[0] * esz);
         L.vel[1] = take((size_t)n[2] * nf[1] * n[0] * esz);
@@ -130,7 +133,7 @@ Layout layout(const ch_params* p) {
     if (p->ncx) {
         const int64_t nc[3] = {p->ncx, p->ncy, p->ncz};
         int64_t ncf[3];
-        for (int d = 0; d < 3; ++d) ncf[d] = nc[d] + (p->bc[d] == CH_NOFLUX ? 1 : 0);
+        for (int d = 0; d < 3; ++d) ncf[d] = nc[d] + (p->bc[d] != CH_PERIODIC ? 1 : 0);
         L.velc[0] = take((size_t)nc[2] * nc[1] * ncf[0] * esz);
         L.velc[1] = take((size_t)nc[2] * ncf[1] * nc[0] * esz);
         L.velc[2] = take((size_t)ncf[2] * nc[1] * nc[0] * esz);
@@ -539,7 +542,7 @@ int ch_create(const ch_params* p, void* C, void* work, size_t work_bytes, void* 
     h->n[0] = p->nx;
     h->n[1] = p->ny;
     h->n[2] = p->nz;
-    for (int d = 0; d < 3; ++d) h->nf[d] = h->n[d] + (p->bc[d] == CH_NOFLUX ? 1 : 0);
+    for (int d = 0; d < 3; ++d) h->nf[d] = h->n[d] + (p->bc[d] != CH_PERIODIC ? 1 : 0);
     h->ncell = p->nx * p->ny * p->nz;
     h->stream = (cudaStream_t)stream;
     h->C = C;
@@ -555,7 +558,7 @@ int ch_create(const ch_params* p, void* C, void* work, size_t work_bytes, void* 
             h->vel_c[d] = wb + L.velc[d];
             h->grad_c[d] = wb + L.gradc[d];
             h->nc[d] = nc[d];
-            h->ncf[d] = nc[d] + (p->bc[d] == CH_NOFLUX ? 1 : 0);
+            h->ncf[d] = nc[d] + (p->bc[d] != CH_PERIODIC ? 1 : 0);
         }
     h->launches_per_step = p->scheme == CH_SCHEME_STANDARD ? (p->advect ? 3 : 2) * kRK : 4 * kRK;
 

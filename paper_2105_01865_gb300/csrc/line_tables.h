@@ -12,7 +12,8 @@
 
 namespace chg {
 
-constexpr int kBcPeriodic = 0;  // same values as CH_PERIODIC / CH_NOFLUX
+constexpr int kBcPeriodic = 0;   // same values as CH_PERIODIC / CH_NOFLUX / CH_DIRICHLET
+constexpr int kBcDirichlet = 2;
 constexpr int kBcNoflux = 1;
 
 // Banded LU without pivoting of a pentadiagonal matrix given by its bands
@@ -103,13 +104,20 @@ inline LineFactors line_factors(int n, int bc, double ck) {
     for (int i = 0; i < n; ++i) {
         for (int s = -2; s <= 2; ++s) {
             int j = i + s;
+            double sign = 1.0;  // a Dirichlet ghost is the negated mirror
             if (F.periodic) {
                 j = ((j % n) + n) % n;
             } else {
-                if (j < 0) j = -1 - j;
-                if (j >= n) j = 2 * n - 1 - j;
+                if (j < 0) {
+                    j = -1 - j;
+                    if (bc == kBcDirichlet) sign = -1.0;
+                }
+                if (j >= n) {
+                    j = 2 * n - 1 - j;
+                    if (bc == kBcDirichlet) sign = -1.0;
+                }
             }
-            const double val = ck * stencil[s + 2];
+            const double val = sign * ck * stencil[s + 2];
             switch (j - i) {
                 case -2: e[i] += val; break;
                 case -1: c[i] += val; break;

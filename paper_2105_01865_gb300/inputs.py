@@ -66,14 +66,14 @@ def shear_velocity(shape, h, gamma_dot, bc):
     """Imposed shear u = gamma_dot (z - 1/2), v = w = 0 on the staggered mesh.
 
     u lives on x-faces at the cell-centre height; walls at z = 0, 1 when
-    bc_z is no-flux (then w has nz + 1 planes, all zero)."""
+    bc_z is a wall (then w has nz + 1 planes, all zero)."""
     nz, ny, nx = shape
-    nfx = nx + (1 if bc[0] == NOFLUX else 0)
-    nfy = ny + (1 if bc[1] == NOFLUX else 0)
-    nfz = nz + (1 if bc[2] == NOFLUX else 0)
+    nfx = nx + (1 if bc[0] != PERIODIC else 0)
+    nfy = ny + (1 if bc[1] != PERIODIC else 0)
+    nfz = nz + (1 if bc[2] != PERIODIC else 0)
     z = cell_centres(nz, h)
     u = np.broadcast_to((gamma_dot * (z - 0.5))[:, None, None], (nz, ny, nfx)).copy()
-    if bc[0] == NOFLUX:
+    if bc[0] != PERIODIC:
         u[:, :, 0] = 0.0
         u[:, :, -1] = 0.0
     v = np.zeros((nz, nfy, nx))
@@ -138,7 +138,7 @@ def curl_velocity(xf, yf, zf, bc, seed, kmax=8, slope=-11.0 / 6.0, umax=1.0):
             out = t if out is None else out + t
         return out
 
-    walled = {d for d in range(3) if bc[d] == NOFLUX}
+    walled = {d for d in range(3) if bc[d] != PERIODIC}
     # a tangential component must vanish on walls normal to another direction
     Ax = component((cents[0], faces[1], faces[2]), walled - {0})
     Ay = component((faces[0], cents[1], faces[2]), walled - {1})

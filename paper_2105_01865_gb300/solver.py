@@ -15,7 +15,7 @@ class Solver:
     """Fine-mesh Cahn-Hilliard solver on one GPU.
 
     shape = (nz, ny, nx); bc = (bc_x, bc_y, bc_z) with capi.CH_PERIODIC /
-    capi.CH_NOFLUX; precision "f32" or "f64".  C0 is a numpy or torch array of
+    capi.CH_NOFLUX (bc_z may also be capi.CH_DIRICHLET); precision "f32" or "f64".  C0 is a numpy or torch array of
     the initial volume fraction.  coarse_faces = (xf, yf, zf) enables the
     velocity transfer from a stretched coarse mesh.  scheme "split" is the
     paper's factorised implicit biharmonic; "standard" the explicit 25-point
@@ -46,11 +46,11 @@ class Solver:
         with torch.cuda.device(self.device):
             self.handle = capi.ch_create(self.params, self.C, self.work, self.stream)
         nz, ny, nx = self.shape
-        nf = [n + (1 if b == capi.CH_NOFLUX else 0) for n, b in zip((nx, ny, nz), self.bc)]
+        nf = [n + (1 if b != capi.CH_PERIODIC else 0) for n, b in zip((nx, ny, nz), self.bc)]
         self.vel_shapes = ((nz, ny, nf[0]), (nz, nf[1], nx), (nf[2], ny, nx))
         if coarse_faces is not None:
             nc = [len(f) - 1 for f in coarse_faces]
-            ncf = [n + (1 if b == capi.CH_NOFLUX else 0) for n, b in zip(nc, self.bc)]
+            ncf = [n + (1 if b != capi.CH_PERIODIC else 0) for n, b in zip(nc, self.bc)]
             self.coarse_shapes = ((nc[2], nc[1], ncf[0]), (nc[2], ncf[1], nc[0]), (ncf[2], nc[1], nc[0]))
 
     def _order(self):

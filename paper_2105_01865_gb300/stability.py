@@ -7,7 +7,7 @@ amplify any grid mode.  With psi' linearised about a state of slope psi'' the
 discrete operators are diagonal in the grid's Fourier (periodic) or cosine
 (mirror-wall) modes: lap_h -> -sum_d s_d, A_d -> w Cn^2 s_d^2 with
 s_d = 4 sin^2(theta_d / 2) / h^2, theta_d = 2 pi m / n (periodic) or
-pi m / n (walls).  Each substep l then maps (q, H^{l-1}) linearly, and the
+pi m / n (walls; m = 1 .. n for Dirichlet walls, whose modes are sines).  Each substep l then maps (q, H^{l-1}) linearly, and the
 step's amplification is the product of the three substep maps.
 
 stable_dt_standard does the same for the explicit comparison scheme of
@@ -23,7 +23,9 @@ RHO = (0.0, -17.0 / 60.0, -5.0 / 12.0)
 
 
 def _thetas(n, bc, max_modes):
-    m = np.arange(n, dtype=np.float64)
+    # periodic: Fourier modes 2 pi m / n; no-flux walls: cosine modes pi m / n,
+    # m = 0 .. n-1; Dirichlet walls: sine modes pi m / n, m = 1 .. n
+    m = np.arange(1, n + 1, dtype=np.float64) if bc == 2 else np.arange(n, dtype=np.float64)
     th = (2.0 if bc == 0 else 1.0) * np.pi * m / n
     if n > max_modes:
         th = np.unique(np.concatenate([th[:: max(1, n // max_modes)], th[-1:]]))

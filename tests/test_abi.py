@@ -43,8 +43,14 @@ def test_workspace_bytes_validates(lib):
     assert n >= 3 * N * 4 + (16 * 12 * 10 + 16 * 12 * 10 + 17 * 12 * 10) * 4
     bad = capi.make_params((16, 12, 4), 0.1, (0, 0, 1), 0.075, 10.0, 1e-3)       # n < 5
     assert capi.ch_workspace_bytes(bad) == 0
-    bad = capi.make_params((16, 12, 10), 0.1, (0, 0, 2), 0.075, 10.0, 1e-3)      # bad bc
+    bad = capi.make_params((16, 12, 10), 0.1, (0, 0, 3), 0.075, 10.0, 1e-3)      # bad bc
     assert capi.ch_workspace_bytes(bad) == 0
+    bad = capi.make_params((16, 12, 10), 0.1, (2, 0, 1), 0.075, 10.0, 1e-3)      # Dirichlet only in z
+    assert capi.ch_workspace_bytes(bad) == 0
+    ok = capi.make_params((16, 12, 10), 0.1, (0, 0, 2), 0.075, 10.0, 1e-3)       # Dirichlet z walls
+    assert capi.ch_workspace_bytes(ok) > 0
+    bad = capi.make_params((16, 12, 10), 0.1, (0, 0, 2), 0.075, 10.0, 1e-3, scheme=capi.CH_SCHEME_STANDARD)
+    assert capi.ch_workspace_bytes(bad) == 0                                      # split scheme only
     bad = capi.make_params((16, 12, 10), 0.1, (0, 0, 1), 0.075, 10.0, -1.0)      # dt <= 0
     assert capi.ch_workspace_bytes(bad) == 0
 
