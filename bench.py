@@ -361,6 +361,39 @@ def scheme_leg(args, dev, W):
     return out
 
 
+def dirichlet_leg(args, dev, flush, W):
+    """The bench's shear-drop box with Dirichlet walls (C = 0 on z = 0, 1, the
+    Rayleigh-Benard setting of Sec. 4.3) instead of no-flux ones: FP32 step
+    time, L2 flushed between steps."""
+    import torch
+    from paper_2105_01865_gb300 import capi, inputs, stability
+    from paper_2105_01865_gb300.solver import Solver
+    f = inputs.shear_drop_box(W["nx"], W["ny"], W["nz"])
+    h, cn, pe = f["h"], f["cn"], f["pe"]
+    bc = (capi.CH_PERIODIC, capi.CH_PERIODIC, capi.CH_DIRICHLET)
+    dt = min(0.9 * stability.stable_dt(f["shape"], h, bc, cn, pe), 0.5 * h / 0.5)
+    s = Solver(f["shape"], h, bc, cn, pe, dt, f["C"], precision="f32", advect=True, device=dev)
+    s.set_velocity_fine(*f["vel"])
+    st = s.stream
+    for _ in range(3):
+        s.step(1)
+    k = max(3, min(args.steps, 20))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+    torch.cuda.synchronize(dev)
+    with torch.cuda.stream(st):
+        for a, b in ev:
+            flush.fill_(1)
+            a.record(st)
+            s.step(1)
+            b.record(st)
+    torch.cuda.synchronize(dev)
+    ms = sum(a.elapsed_time(b) for a, b in ev) / k
+    cells = W["nx"] * W["ny"] * W["nz"]
+    s.close()
+    return dict(value=cells / (ms * 1e-3), unit="cell-updates/s", ms_per_step=ms, steps=k, dtype="f32",
+                bc="x, y periodic; z Dirichlet walls (C = 0)")
+
+
 def gpu_arm(args):
     import torch
     import torch.distributed as dist
@@ -482,6 +515,7 @@ def gpu_arm(args):
     batched = batched_leg(args, dev, flush, rank, world)
     multires = multires_leg(args, dev, flush) if not args.no_multires else None
     schemes = scheme_leg(args, dev, W) if not args.no_scheme else None
+    dirichlet = dirichlet_leg(args, dev, flush, W) if not args.no_scheme else None
     clk.__exit__(None, None, None)
     clocks = clk.summary()
 
@@ -499,7 +533,7 @@ def gpu_arm(args):
                             parallelism=f"replicas{world}", cells=ncell, precision="f32 fields, f64 reductions",
                             l2="flushed between timed steps (256 MB write); working set 235 MB > L2"),
                 roofline=roofline, e2e=e2e, fp64_plain=fp64, batched=batched, multires=multires,
-                scheme_comparison=schemes, clocks=clocks,
+                scheme_comparison=schemes, dirichlet_walls=dirichlet, clocks=clocks,
                 gpu_launches=args.steps * s32.launches_per_step())
     if rank == 0 and not args.no_cpu_baseline:
         cells, times = run_oracle(1, 0)
@@ -524,7 +558,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-multires", action="store_true", help="skip the 1024x1024x512 transfer + step leg")
-    ap.add_argument("--no-scheme", action="store_true", help="skip the split vs standard scheme comparison")
+    ap.add_argument("--no-scheme", action="store_true",
+                    help="skip the split vs standard scheme comparison and the Dirichlet-wall leg")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
