@@ -25,6 +25,21 @@ namespace {
 constexpr size_t kAlign = 256;
 constexpr size_t kMaxSmem = 227 * 1024;  // dynamic shared memory per CTA (sm_103a)
 
+// Use the two-column form of the column solver when nx is even, and its
+// cluster form for y/z lines longer than 256 cells.
+#ifndef CH_COLUMN_PAIRS
+#define CH_COLUMN_PAIRS 1
+#endif
+#ifndef CH_COLUMN_CLUSTER
+#define CH_COLUMN_CLUSTER 1
+#endif
+// Lines of 513..1024 cells over clusters of 4 CTAs: measured slower than the
+// shared-memory tile solver on the 1024-cell periodic y-lines of the
+// 1024x1024x512 box (3.74 against 2.81 ms), so off by default.
+#ifndef CH_COLUMN_CLUSTER4
+#define CH_COLUMN_CLUSTER4 0
+#endif
+
 // Launch a step kernel, optionally with programmatic stream serialisation
 // (CH_PDL = 1): it may then be scheduled while its predecessor on the stream
 // drains, and waits (pdl_wait) before touching memory.  Off by default: on the
@@ -206,6 +221,8 @@ CCoef<T> ccoef(const LineTables& lt) {
     k.Wp = b + L.Wp;
     k.Zp = b + L.Zp;
     k.K = b + L.K;
+    k.PC = b + L.PC;
+    k.QC = b + L.QC;
     k.n = lt.n;
     k.periodic = lt.periodic;
     return k;
@@ -250,6 +267,47 @@ int launch_cols2_rn(ch_handle* h, int l, int dir, T* r, T* Cupd) {
     return CH_OK;
 }
 
+// Cluster form: CL CTAs of NW warps per 64-line tile (lines of up to CL NW R cells).
+template <typename T, int R, int NW, int CL, bool UPDATE>
+int cols2c_launch(ch_handle* h, T* r, T* Cupd, int nx, int64_t outer_stride, int64_t line_stride, int64_t tiles,
+                  const CCoef<T>& cf) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(tiles * CL));
+    cfg.blockDim = dim3(NW * 32);
+    cfg.dynamicSmemBytes = Cols2cSmem<T, R, NW, CL, UPDATE>::kBytes;
+    cfg.stream = h->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CHG_CUDA(h, cudaLaunchKernelEx(&cfg, ch_solve_cols2c<T, R, NW, CL, UPDATE>, r, Cupd, nx, outer_stride,
+                                   line_stride, cf, h->status));
+    return CH_OK;
+}
+
+template <typename T, int R, int NW, int CL>
+int launch_cols2c_rn(ch_handle* h, int l, int dir, T* r, T* Cupd) {
+    const int nx = (int)h->n[0], ny = (int)h->n[1], nz = (int)h->n[2];
+    const CCoef<T> cf = ccoef<T>(h->lines[dir][l]);
+    const int64_t xblocks = (nx + 63) / 64;
+    if (dir == 1)
+        return cols2c_launch<T, R, NW, CL, false>(h, r, nullptr, nx, (int64_t)nx * ny, nx, xblocks * nz, cf);
+    if (Cupd) return cols2c_launch<T, R, NW, CL, true>(h, r, Cupd, nx, nx, (int64_t)nx * ny, xblocks * ny, cf);
+    return cols2c_launch<T, R, NW, CL, false>(h, r, nullptr, nx, nx, (int64_t)nx * ny, xblocks * ny, cf);
+}
+
+template <typename T, int R, int NW, int CL>
+int set_attrs_cols2c(ch_handle* h) {
+    CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_cols2c<T, R, NW, CL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)Cols2cSmem<T, R, NW, CL, false>::kBytes));
+    CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_cols2c<T, R, NW, CL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)Cols2cSmem<T, R, NW, CL, true>::kBytes));
+    return CH_OK;
+}
+
 template <typename T, int R, int NW>
 int set_attrs_cols2(ch_handle* h) {
     CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_cols2<T, R, NW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -269,6 +327,8 @@ int set_attrs_cols2_all(ch_handle* h) {
     if (rc == CH_OK) rc = set_attrs_cols2<T, 16, 16>(h);
     if (rc == CH_OK) rc = set_attrs_cols2<T, 8, 16>(h);
     if (rc == CH_OK) rc = set_attrs_cols2<T, 8, 32>(h);
+    if (rc == CH_OK) rc = set_attrs_cols2c<T, 16, kClusterNW, 2>(h);
+    if (rc == CH_OK) rc = set_attrs_cols2c<T, 16, kClusterNW, 4>(h);
     return rc;
 }
 
@@ -278,10 +338,7 @@ int set_attrs_cols2_all(ch_handle* h) {
 #ifndef CH_COLUMN_DIRS
 #define CH_COLUMN_DIRS 6
 #endif
-// Use the two-column form of the column solver when nx is even.
-#ifndef CH_COLUMN_PAIRS
-#define CH_COLUMN_PAIRS 1
-#endif
+
 
 // Column solver for y/z lines (shape chosen by col_shape); -1 if none.
 template <typename T>
@@ -304,6 +361,10 @@ int launch_cols(ch_handle* h, int l, int dir, T* r, T* Cupd) {
             if (lt.nw == 16 && lt.R == 16) return launch_cols2_rn<T, 16, 16>(h, l, dir, r, Cupd);
             if (lt.nw == 16 && lt.R == 8) return launch_cols2_rn<T, 8, 16>(h, l, dir, r, Cupd);
             if (lt.nw == 32 && lt.R == 8) return launch_cols2_rn<T, 8, 32>(h, l, dir, r, Cupd);
+            if (CH_COLUMN_CLUSTER && lt.R == 16 && lt.nw == 2 * kClusterNW)
+                return launch_cols2c_rn<T, 16, kClusterNW, 2>(h, l, dir, r, Cupd);
+            if (CH_COLUMN_CLUSTER && lt.R == 16 && lt.nw == 4 * kClusterNW)
+                return launch_cols2c_rn<T, 16, kClusterNW, 4>(h, l, dir, r, Cupd);
             // 32 warps leave 64 registers a thread: the one-column form below
         }
     }
@@ -597,7 +658,9 @@ int ch_create(const ch_params* p, void* C, void* work, size_t work_bytes, void* 
                 total += align_up(all.back().size() * h->esz);
                 // y and z lines also get column-solver tables when they fit
                 int nw = 0, R = 0;
-                if (d > 0 && col_shape(n, &nw, &R)) {
+                // lines over 512 cells run the column solver only in its cluster form (FP32, even nx)
+                const bool cluster_ok = CH_COLUMN_PAIRS && CH_COLUMN_CLUSTER && h->esz == 4 && h->n[0] % 2 == 0;
+                if (d > 0 && col_shape(n, &nw, &R) && (nw <= 32 || (cluster_ok && CH_COLUMN_CLUSTER4))) {
                     lt.nw = nw;
                     lt.R = R;
                     all.push_back(col_tables(F, nw, R));

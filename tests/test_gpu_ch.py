@@ -222,16 +222,25 @@ def test_graph_replay_matches_direct_launches():
     assert np.array_equal(a.field(), b.field())
 
 
-@pytest.mark.parametrize("shape,bc", [((6, 600, 8), (co.PERIODIC, co.PERIODIC, co.NOFLUX)),
-                                      ((560, 5, 6), (co.NOFLUX, co.NOFLUX, co.PERIODIC))])
-def test_fp32_long_lines_use_the_tile_solver(shape, bc):
-    """Lines longer than 512 cells take the shared-memory tile solver."""
+@pytest.mark.parametrize("shape,bc,prec", [
+    ((6, 600, 8), (co.PERIODIC, co.PERIODIC, co.NOFLUX), "f32"),   # y 600: shared-memory tile solver
+    ((560, 5, 6), (co.NOFLUX, co.NOFLUX, co.PERIODIC), "f32"),     # z 560 periodic + update: tile solver
+    ((6, 300, 10), (co.PERIODIC, co.PERIODIC, co.NOFLUX), "f32"),  # y 300 periodic: cluster of 2
+    ((400, 6, 6), (co.PERIODIC, co.NOFLUX, co.NOFLUX), "f32"),     # z 400 walls + update: cluster of 2
+    ((6, 600, 7), (co.PERIODIC, co.PERIODIC, co.NOFLUX), "f32"),   # odd nx: shared-memory tile solver
+    ((6, 300, 8), (co.PERIODIC, co.PERIODIC, co.NOFLUX), "f64"),   # FP64: one-column form
+])
+def test_long_lines(shape, bc, prec):
+    """Lines longer than 256 cells: up to 512, the cluster form of the
+    two-column solver (FP32, even nx) or the one-column form; beyond, the tile
+    solver."""
     h = 1.0 / 64
     cn = 0.75 * h
     rng = np.random.default_rng(17)
     C0 = 0.5 + 0.2 * rng.standard_normal(shape)
     dt = 2e-4
-    s = make(shape, h, bc, cn, 50.0, dt, C0, "f32")
+    s = make(shape, h, bc, cn, 50.0, dt, C0, prec)
     s.step(3)
-    ref = co.step(C0, None, oracle_params(shape, h, bc, cn, 50.0, dt), 3)
-    assert rel_l2(s.field(), ref) <= 1e-6
+    ref = co.step(C0.astype(np.float32).astype(np.float64) if prec == "f32" else C0, None,
+                  oracle_params(shape, h, bc, cn, 50.0, dt), 3)
+    assert rel_l2(s.field(), ref) <= (1e-6 if prec == "f32" else 1e-12)
