@@ -162,7 +162,9 @@ constexpr int kHL2 = 4;   // left halo columns (even, so thread pairs stay 8/16-
 // One 64 x 8 x zchunk tile (tile coordinates bx, by, bz) computed by the 256
 // threads of a CTA; called by the standalone kernel below and by the batched
 // persistent kernel.
-template <typename T, bool ADV>
+template <typename T, bool ADV, bool DIRI = false>
+// DIRI: compiled for Dirichlet z-walls (negated ghost planes); false for every
+// other wall type, which then carries no extra code.
 // Data pointers carry no __restrict__ here: the batched persistent kernel
 // writes these arrays in one phase and reads them in the next, so their loads
 // must not go through the non-coherent read-only path.
@@ -213,7 +215,7 @@ __device__ __forceinline__ void explicit_tile2(const T* C, const T* u, const T* 
 #pragma unroll
     for (int m = 0; m < 6; ++m) {
         q[m] = ldp(C + (bc_near(k0 - 2 + m, a.nz, a.bcz) * plane + col));
-        if (bc_negate(k0 - 2 + m, a.nz, a.bcz)) q[m] = sub(sp<T>(T(0)), q[m]);
+        if (DIRI && bc_negate(k0 - 2 + m, a.nz, a.bcz)) q[m] = sub(sp<T>(T(0)), q[m]);
     }
 
     Pr<T> fz_lo = sp<T>(T(0));
@@ -221,7 +223,7 @@ __device__ __forceinline__ void explicit_tile2(const T* C, const T* u, const T* 
         const bool wall = (a.bcz != CH_PERIODIC) && (k0 == 0);
         if (!wall) {
             Pr<T> cm3 = ldp(C + (bc_near(k0 - 3, a.nz, a.bcz) * plane + col));
-            if (bc_negate(k0 - 3, a.nz, a.bcz)) cm3 = sub(sp<T>(T(0)), cm3);
+            if (DIRI && bc_negate(k0 - 3, a.nz, a.bcz)) cm3 = sub(sp<T>(T(0)), cm3);
             const Pr<T> wv = ldp(w + (k0 * plane + col));
             fz_lo = face_flux_p(wv, cm3, q[0], q[1], q[2], q[3], q[4], eps);
         }
@@ -269,7 +271,7 @@ __device__ __forceinline__ void explicit_tile2(const T* C, const T* u, const T* 
         }
         // per-thread global inputs of this plane (issued before the barrier)
         Pr<T> qnext = ldp(C + (bc_near(k + 4, a.nz, a.bcz) * plane + col));
-        if (bc_negate(k + 4, a.nz, a.bcz)) qnext = sub(sp<T>(T(0)), qnext);
+        if (DIRI && bc_negate(k + 4, a.nz, a.bcz)) qnext = sub(sp<T>(T(0)), qnext);
         const int kp = k * a.ny;
         T uxa = T(0), uxb = T(0), uxe_a = T(0), uxe_b = T(0);
         Pr<T> vy = sp<T>(T(0)), vye = sp<T>(T(0)), wz = sp<T>(T(0)), hp = sp<T>(T(0));
@@ -339,7 +341,7 @@ __device__ __forceinline__ void explicit_tile2(const T* C, const T* u, const T* 
         const Pr<T> xl = mk(s3, s4), xr = mk(s5, s6);
         const Pr<T> pc = psi_pp(c0);
         Pr<T> pzm = psi_pp(q[1]), pzp = psi_pp(q[3]);
-        if (a.bcz == CH_DIRICHLET) {  // the ghost of psi' is its own negated mirror (psi' = 0 on the wall)
+        if (DIRI && a.bcz == CH_DIRICHLET) {  // the ghost of psi' is its own negated mirror (psi' = 0 on the wall)
             if (k == 0) pzm = sub(sp<T>(T(0)), psi_pp(sub(sp<T>(T(0)), q[1])));
             if (k + 1 == a.nz) pzp = sub(sp<T>(T(0)), psi_pp(sub(sp<T>(T(0)), q[3])));
         }
@@ -379,14 +381,14 @@ __device__ __forceinline__ void explicit_tile2(const T* C, const T* u, const T* 
     }
 }
 
-template <typename T, bool ADV>
+template <typename T, bool ADV, bool DIRI>
 __global__ void __launch_bounds__(32 * kTY, sizeof(T) == 4 ? CH_EXPLICIT_MIN_BLOCKS : 2)
 ch_explicit_rhs2(const T* __restrict__ C, const T* __restrict__ u, const T* __restrict__ v,
                  const T* __restrict__ w, const T* __restrict__ Hprev, T* __restrict__ Hout, T* __restrict__ r,
                  RhsArgs<T> a) {
     pdl_wait();
     pdl_launch_dependents();
-    explicit_tile2<T, ADV>(C, u, v, w, Hprev, Hout, r, a, blockIdx.x, blockIdx.y, blockIdx.z, kTZ2);
+    explicit_tile2<T, ADV, DIRI>(C, u, v, w, Hprev, Hout, r, a, blockIdx.x, blockIdx.y, blockIdx.z, kTZ2);
 }
 
 }  // namespace chg

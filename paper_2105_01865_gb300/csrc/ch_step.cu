@@ -458,10 +458,19 @@ int launch_explicit(ch_handle* h, int l, const T* C, const T* Hprev, T* Hout, T*
     if (nx % 2 == 0) {  // two cells per thread (paired FP32 arithmetic)
         dim3 grid((nx + kTX2 - 1) / kTX2, (ny + kTY - 1) / kTY, (nz + kTZ2 - 1) / kTZ2);
         dim3 block(32, kTY);
-        if (p.advect)
-            launch_k(h->stream, ch_explicit_rhs2<T, true>, dim3(grid), dim3(block), 0, C, u, v, w, Hprev, Hout, r, a);
+        const bool diri = p.bc[2] == CH_DIRICHLET;
+        if (p.advect && diri)
+            launch_k(h->stream, ch_explicit_rhs2<T, true, true>, dim3(grid), dim3(block), 0, C, u, v, w, Hprev, Hout, r,
+                     a);
+        else if (p.advect)
+            launch_k(h->stream, ch_explicit_rhs2<T, true, false>, dim3(grid), dim3(block), 0, C, u, v, w, Hprev, Hout,
+                     r, a);
+        else if (diri)
+            launch_k(h->stream, ch_explicit_rhs2<T, false, true>, dim3(grid), dim3(block), 0, C, u, v, w, Hprev, Hout,
+                     r, a);
         else
-            launch_k(h->stream, ch_explicit_rhs2<T, false>, dim3(grid), dim3(block), 0, C, u, v, w, Hprev, Hout, r, a);
+            launch_k(h->stream, ch_explicit_rhs2<T, false, false>, dim3(grid), dim3(block), 0, C, u, v, w, Hprev, Hout,
+                     r, a);
     } else {
         dim3 grid((nx + kTX - 1) / kTX, (ny + kTY - 1) / kTY, (nz + kTZ - 1) / kTZ);
         dim3 block(kTX, kTY);
