@@ -575,8 +575,6 @@ int ch_batch_create(const ch_params* boxes, int nbox, void* const* C, void* work
                         c.Wp = base + L.Wp;
                         c.Zp = base + L.Zp;
                         c.K = base + L.K;
-                        c.PC = base + L.PC;
-                        c.QC = base + L.QC;
                         c.n = nd;
                         c.periodic = per;
                         off += align256(t.size() * sizeof(float));

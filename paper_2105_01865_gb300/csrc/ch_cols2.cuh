@@ -234,7 +234,7 @@ ch_solve_cols2(T* __restrict__ a, T* __restrict__ Cf, int nx, int64_t outer_stri
 // CTA publishes its zero-start total state, and after a cluster barrier CTA r
 // reads the totals of the CTAs before it (forward) or after it (backward)
 // from their shared memory (distributed shared memory) and composes them with
-// the host-precomputed per-CTA products PC, QC.  Periodic lines read the four
+// the products of those CTAs' warp matrices, which each CTA also publishes.  Periodic lines read the four
 // corner rows from the CTAs that own them the same way.  A last cluster
 // barrier keeps every CTA's shared memory alive until the remote reads end.
 // ---------------------------------------------------------------------------
@@ -250,7 +250,7 @@ struct Cols2cSmem {
 };
 
 template <typename T, int R, int NW, int CL, bool UPDATE>
-__global__ void __launch_bounds__(NW * 32, 1)
+__global__ void __launch_bounds__(NW * 32, Cols2MinBlocks<R, NW>::value)
 ch_solve_cols2c(T* __restrict__ a, T* __restrict__ Cf, int nx, int64_t outer_stride, int64_t line_stride,
                 CCoef<T> cf, unsigned int* status) {
     namespace cg = cooperative_groups;
@@ -262,6 +262,7 @@ ch_solve_cols2c(T* __restrict__ a, T* __restrict__ Cf, int nx, int64_t outer_str
     Pr<T>* tot = bq + NW * 2 * 32;                   // [2 (fwd, bwd)][2][32]
     Pr<T>* corner = tot + 2 * 2 * 32;                // [4][32]
     Pr<T>* cbuf = corner + 4 * 32;                   // [rows of this CTA][32]
+    __shared__ T prod[8];                            // this CTA's forward and backward matrix products
     const int rank = (int)cluster.block_rank();
     const int64_t tile = blockIdx.x / CL;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -302,26 +303,34 @@ ch_solve_cols2c(T* __restrict__ a, T* __restrict__ Cf, int nx, int64_t outer_str
     fq[(w * 2 + 0) * 32 + lane] = y1;
     fq[(w * 2 + 1) * 32 + lane] = y2;
     __syncthreads();
-    if (w == 0) {  // this CTA's zero-start total
+    if (w == 0) {  // this CTA's zero-start total and the product of its warps' matrices
         Pr<T> t0 = sp<T>(T(0)), t1 = sp<T>(T(0));
+        T p00 = T(1), p01 = T(0), p10 = T(0), p11 = T(1);
         for (int u = 0; u < NW; ++u) {
             const V4<T> Pm = ld4(cf.P + 4 * (gw0 + u));
             const Pr<T> n0 = fma2(sp<T>(Pm.x), t0, fma2(sp<T>(Pm.y), t1, fq[(u * 2 + 0) * 32 + lane]));
             const Pr<T> n1 = fma2(sp<T>(Pm.z), t0, fma2(sp<T>(Pm.w), t1, fq[(u * 2 + 1) * 32 + lane]));
             t0 = n0;
             t1 = n1;
+            const T q00 = Pm.x * p00 + Pm.y * p10, q01 = Pm.x * p01 + Pm.y * p11;
+            const T q10 = Pm.z * p00 + Pm.w * p10, q11 = Pm.z * p01 + Pm.w * p11;
+            p00 = q00; p01 = q01; p10 = q10; p11 = q11;
         }
         tot[0 * 32 + lane] = t0;
         tot[1 * 32 + lane] = t1;
+        if (lane == 0) {
+            prod[0] = p00; prod[1] = p01; prod[2] = p10; prod[3] = p11;
+        }
     }
     cluster.sync();
     // incoming state: the totals of the CTAs before this one, then this CTA's warps before w
     Pr<T> s0 = sp<T>(T(0)), s1 = sp<T>(T(0));
     for (int c = 0; c < rank; ++c) {
         const Pr<T>* rt = cluster.map_shared_rank(tot, c);
-        const V4<T> Pm = ld4(cf.PC + 4 * c);
-        const Pr<T> n0 = fma2(sp<T>(Pm.x), s0, fma2(sp<T>(Pm.y), s1, rt[0 * 32 + lane]));
-        const Pr<T> n1 = fma2(sp<T>(Pm.z), s0, fma2(sp<T>(Pm.w), s1, rt[1 * 32 + lane]));
+        const T* rp = cluster.map_shared_rank(prod, c);
+        const T m00 = rp[0], m01 = rp[1], m10 = rp[2], m11 = rp[3];
+        const Pr<T> n0 = fma2(sp<T>(m00), s0, fma2(sp<T>(m01), s1, rt[0 * 32 + lane]));
+        const Pr<T> n1 = fma2(sp<T>(m10), s0, fma2(sp<T>(m11), s1, rt[1 * 32 + lane]));
         s0 = n0;
         s1 = n1;
     }
@@ -359,26 +368,34 @@ ch_solve_cols2c(T* __restrict__ a, T* __restrict__ Cf, int nx, int64_t outer_str
     bq[(w * 2 + 1) * 32 + lane] = x2;
     if (UPDATE) cp_async_wait<0>();
     __syncthreads();
-    if (w == NW - 1) {  // this CTA's zero-start backward total
+    if (w == NW - 1) {  // this CTA's zero-start backward total and the product of its warps' matrices
         Pr<T> t0 = sp<T>(T(0)), t1 = sp<T>(T(0));
+        T p00 = T(1), p01 = T(0), p10 = T(0), p11 = T(1);
         for (int u = NW - 1; u >= 0; --u) {
             const V4<T> Qm = ld4(cf.Q + 4 * (gw0 + u));
             const Pr<T> n0 = fma2(sp<T>(Qm.x), t0, fma2(sp<T>(Qm.y), t1, bq[(u * 2 + 0) * 32 + lane]));
             const Pr<T> n1 = fma2(sp<T>(Qm.z), t0, fma2(sp<T>(Qm.w), t1, bq[(u * 2 + 1) * 32 + lane]));
             t0 = n0;
             t1 = n1;
+            const T q00 = Qm.x * p00 + Qm.y * p10, q01 = Qm.x * p01 + Qm.y * p11;
+            const T q10 = Qm.z * p00 + Qm.w * p10, q11 = Qm.z * p01 + Qm.w * p11;
+            p00 = q00; p01 = q01; p10 = q10; p11 = q11;
         }
         tot[2 * 32 + lane] = t0;
         tot[3 * 32 + lane] = t1;
+        if (lane == 0) {
+            prod[4] = p00; prod[5] = p01; prod[6] = p10; prod[7] = p11;
+        }
     }
     cluster.sync();
     s0 = sp<T>(T(0));
     s1 = sp<T>(T(0));
     for (int c = CL - 1; c > rank; --c) {
         const Pr<T>* rt = cluster.map_shared_rank(tot, c);
-        const V4<T> Qm = ld4(cf.QC + 4 * c);
-        const Pr<T> n0 = fma2(sp<T>(Qm.x), s0, fma2(sp<T>(Qm.y), s1, rt[2 * 32 + lane]));
-        const Pr<T> n1 = fma2(sp<T>(Qm.z), s0, fma2(sp<T>(Qm.w), s1, rt[3 * 32 + lane]));
+        const T* rp = cluster.map_shared_rank(prod, c);
+        const T m00 = rp[4], m01 = rp[5], m10 = rp[6], m11 = rp[7];
+        const Pr<T> n0 = fma2(sp<T>(m00), s0, fma2(sp<T>(m01), s1, rt[2 * 32 + lane]));
+        const Pr<T> n1 = fma2(sp<T>(m10), s0, fma2(sp<T>(m11), s1, rt[3 * 32 + lane]));
         s0 = n0;
         s1 = n1;
     }

@@ -750,8 +750,6 @@ struct CCoef {
     const T* __restrict__ Wp;     // [rows][8]: W_m (x2), periodic only
     const T* __restrict__ Zp;     // [rows][8]: -Z_m (x2), periodic only
     const T* __restrict__ K;      // [4][4] corner-form correction, periodic only
-    const T* __restrict__ PC;     // [CTA][4] product of a CTA's warp matrices (cluster form)
-    const T* __restrict__ QC;     // [CTA][4]
     int n;
     int periodic;
 };

@@ -39,6 +39,11 @@ constexpr size_t kMaxSmem = 227 * 1024;  // dynamic shared memory per CTA (sm_10
 #ifndef CH_COLUMN_CLUSTER4
 #define CH_COLUMN_CLUSTER4 0
 #endif
+// Lines of 65..256 cells also over 2-CTA clusters (CTAs of 4 or 8 warps), so
+// that two tiles share an SM.
+#ifndef CH_COLUMN_CLUSTER_SMALL
+#define CH_COLUMN_CLUSTER_SMALL 0
+#endif
 
 // Launch a step kernel, optionally with programmatic stream serialisation
 // (CH_PDL = 1): it may then be scheduled while its predecessor on the stream
@@ -221,8 +226,6 @@ CCoef<T> ccoef(const LineTables& lt) {
     k.Wp = b + L.Wp;
     k.Zp = b + L.Zp;
     k.K = b + L.K;
-    k.PC = b + L.PC;
-    k.QC = b + L.QC;
     k.n = lt.n;
     k.periodic = lt.periodic;
     return k;
@@ -328,6 +331,8 @@ int set_attrs_cols2_all(ch_handle* h) {
     if (rc == CH_OK) rc = set_attrs_cols2<T, 8, 16>(h);
     if (rc == CH_OK) rc = set_attrs_cols2<T, 8, 32>(h);
     if (rc == CH_OK) rc = set_attrs_cols2c<T, 16, kClusterNW, 2>(h);
+    if (rc == CH_OK) rc = set_attrs_cols2c<T, 16, 8, 2>(h);
+    if (rc == CH_OK) rc = set_attrs_cols2c<T, 16, 4, 2>(h);
     if (rc == CH_OK) rc = set_attrs_cols2c<T, 16, kClusterNW, 4>(h);
     return rc;
 }
@@ -348,6 +353,10 @@ int launch_cols(ch_handle* h, int l, int dir, T* r, T* Cupd) {
     // two-column form: FP32 only (an FP64 lane would hold 4 R registers of rows)
     if constexpr (sizeof(T) == 4) {
         if (CH_COLUMN_PAIRS && h->n[0] % 2 == 0) {
+            if (CH_COLUMN_CLUSTER_SMALL && lt.R == 16 && lt.nw == 16)
+                return launch_cols2c_rn<T, 16, 8, 2>(h, l, dir, r, Cupd);
+            if (CH_COLUMN_CLUSTER_SMALL && lt.R == 16 && lt.nw == 8)
+                return launch_cols2c_rn<T, 16, 4, 2>(h, l, dir, r, Cupd);
             if (lt.nw == 8) {
                 switch (lt.R) {
                     case 1: return launch_cols2_rn<T, 1, 8>(h, l, dir, r, Cupd);

@@ -309,14 +309,12 @@ struct ColLayout {
     size_t fwd, bwd, W, Z, P, Q, S;
     size_t fwdp, dinvp, bwdp, Wp, Zp;  // the same rows as duplicated pairs (two-column form)
     size_t K;                          // corner-form correction matrix (two-column form)
-    size_t PC, QC;                     // per-CTA products of 16 warps' P (Q), for lines split over a cluster
     size_t total;
 };
 
-// Cluster form of the two-column solver: CTAs of kClusterNW warps, at most
-// kClusterMax CTAs per line.
+// Cluster form of the two-column solver: lines of 257..1024 cells over CTAs
+// of kClusterNW warps.
 constexpr int kClusterNW = 16;
-constexpr int kClusterMax = 4;
 
 inline ColLayout col_layout(int nw, int R) {
     ColLayout L;
@@ -335,8 +333,6 @@ inline ColLayout col_layout(int nw, int R) {
     L.Wp = off;    off += rows * 8;
     L.Zp = off;    off += rows * 8;
     L.K = off;     off += 16;
-    L.PC = off;    off += 4 * kClusterMax;
-    L.QC = off;    off += 4 * kClusterMax;
     L.total = (off + 63) / 64 * 64;
     return L;
 }
@@ -384,17 +380,6 @@ inline std::vector<double> col_tables(const LineFactors& F, int nw, int R) {
         for (int m = 0; m < 4; ++m) {
             t[L.P + 4 * (size_t)w + m] = p[m];
             t[L.Q + 4 * (size_t)w + m] = q[m];
-        }
-    }
-    // per-CTA products for a line split over CTAs of kClusterNW warps:
-    // PC_c = P_last ... P_first (forward), QC_c = Q_first ... Q_last (backward)
-    for (int c = 0; c < kClusterMax && (c + 1) * kClusterNW <= nw; ++c) {
-        double pc[4] = {1, 0, 0, 1}, qc[4] = {1, 0, 0, 1};
-        for (int u = c * kClusterNW; u < (c + 1) * kClusterNW; ++u) mat2_mul(&t[L.P + 4 * (size_t)u], pc, pc);
-        for (int u = (c + 1) * kClusterNW - 1; u >= c * kClusterNW; --u) mat2_mul(&t[L.Q + 4 * (size_t)u], qc, qc);
-        for (int m = 0; m < 4; ++m) {
-            t[L.PC + 4 * (size_t)c + m] = pc[m];
-            t[L.QC + 4 * (size_t)c + m] = qc[m];
         }
     }
     if (F.periodic)
