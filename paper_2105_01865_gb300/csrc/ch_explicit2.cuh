@@ -155,6 +155,9 @@ __device__ __forceinline__ Pr<T> face_flux_p(Pr<T> vel, Pr<T> m3, Pr<T> m2, Pr<T
 #ifndef CH_EXPLICIT_STAGE_OFFSETS
 #define CH_EXPLICIT_STAGE_OFFSETS 1
 #endif
+#ifndef CH_EXPLICIT_PREFETCH
+#define CH_EXPLICIT_PREFETCH 1
+#endif
 constexpr int kTX2 = 64;               // cells in x per CTA (two per thread)
 constexpr int kTZ2 = CH_EXPLICIT_TZ;   // z-planes marched per CTA
 constexpr int kHL2 = 4;   // left halo columns (even, so thread pairs stay 8/16-byte aligned)
@@ -176,6 +179,16 @@ __device__ __forceinline__ void explicit_tile2(const T* C, const T* u, const T* 
     __shared__ __align__(16) T Fx[ADV ? kTY : 1][kTX2 + 2];
     __shared__ __align__(16) T Fy[ADV ? kTY + 1 : 1][kTX2];
     __shared__ int gi_tab[PX], gj_tab[PY];
+    // FP32 with advection: the face velocities and H^{l-1} a thread uses on a
+    // plane are copied by cp.async into its own shared slots one plane ahead,
+    // in the commit group of that plane's C, so no global load latency is
+    // exposed after the plane barrier.  Slot s of thread t holds a pair at
+    // [s][2t]: 0 (u_a, u_b), 1 v, 2 w, 3 H^{l-1}, 4 the extra face's velocity.
+    // Two buffers suffice: a thread consumes every slot it reads before it
+    // issues the next plane's copies.
+    constexpr bool kSlots = CH_EXPLICIT_PREFETCH && ADV && sizeof(T) == 4;
+    constexpr int kNT = 32 * kTY;
+    __shared__ __align__(16) T Ps[kSlots ? 2 : 1][kSlots ? 5 : 1][kSlots ? 2 * kNT : 2];
 
     const int tid = threadIdx.x + threadIdx.y * 32, tx = tid & 31, ty = tid >> 5;
     const int i0 = bx * kTX2, j0 = by * kTY, k0 = bz * zchunk;
@@ -230,6 +243,28 @@ __device__ __forceinline__ void explicit_tile2(const T* C, const T* u, const T* 
     }
     __syncthreads();  // index tables ready
 
+    auto prefetch = [&](int kk) {
+        if constexpr (kSlots) {
+            float* S = reinterpret_cast<float*>(&Ps[(kk - k0) & 1][0][2 * tid]);
+            const float* uf = reinterpret_cast<const float*>(u);
+            const float* vf = reinterpret_cast<const float*>(v);
+            const float* wf = reinterpret_cast<const float*>(w);
+            const int kp = kk * a.ny;
+            if (!wxa) cp_async_elem(S, uf + ((kp + jc) * a.nfx + fxa));
+            if (!wxb) cp_async_elem(S + 1, uf + ((kp + jc) * a.nfx + fxb));
+            if (!wy) cp_async_pair(S + 2 * kNT, vf + ((kk * a.nfy + fy) * a.nx + ic));
+            if (a.bcz == CH_PERIODIC || kk + 1 < a.nz)
+                cp_async_pair(S + 4 * kNT, wf + (((kk + 1 < a.nz) ? kk + 1 : 0) * plane + col));
+            if (a.has_prev && in_xy)
+                cp_async_pair(S + 6 * kNT, reinterpret_cast<const float*>(Hprev) + (kk * plane + j * a.nx + ia));
+            if (ty == 0 && !wye) cp_async_pair(S + 8 * kNT, vf + ((kk * a.nfy + fye) * a.nx + ic));
+            if (ty == 1 && tx < 4 && !wxe) {
+                cp_async_elem(S + 8 * kNT, uf + ((kp + jea) * a.nfx + fxe));
+                cp_async_elem(S + 8 * kNT + 1, uf + ((kp + jeb) * a.nfx + fxe));
+            }
+        }
+    };
+
 #if CH_EXPLICIT_STAGE_OFFSETS
     // in-plane source offsets of this thread's staged elements e = tid + 256 m,
     // the same for every plane of the tile
@@ -249,6 +284,7 @@ __device__ __forceinline__ void explicit_tile2(const T* C, const T* u, const T* 
             const int e = tid + m * 32 * kTY;
             if (e < PX * PY) cp_async_elem(dst + e, Ck + soff[m]);
         }
+        prefetch(kk);
         cp_async_commit();
     };
 #else
@@ -258,6 +294,7 @@ __device__ __forceinline__ void explicit_tile2(const T* C, const T* u, const T* 
             const int row = e / PX, cc = e - row * PX;
             cp_async_elem(&Cs[b][row][cc], Ck + (int64_t)gj_tab[row] * a.nx + gi_tab[cc]);
         }
+        prefetch(kk);
         cp_async_commit();
     };
 #endif
@@ -276,7 +313,7 @@ __device__ __forceinline__ void explicit_tile2(const T* C, const T* u, const T* 
         T uxa = T(0), uxb = T(0), uxe_a = T(0), uxe_b = T(0);
         Pr<T> vy = sp<T>(T(0)), vye = sp<T>(T(0)), wz = sp<T>(T(0)), hp = sp<T>(T(0));
         const bool zwall = (a.bcz != CH_PERIODIC) && (k + 1 >= a.nz);
-        if (ADV) {
+        if (ADV && !kSlots) {
             uxa = wxa ? T(0) : u[(kp + jc) * a.nfx + fxa];
             uxb = wxb ? T(0) : u[(kp + jc) * a.nfx + fxb];
             if (!wy) vy = ldp(v + ((k * a.nfy + fy) * a.nx + ic));
@@ -287,8 +324,21 @@ __device__ __forceinline__ void explicit_tile2(const T* C, const T* u, const T* 
             }
             if (!zwall) wz = ldp(w + (((k + 1 < a.nz) ? k + 1 : 0) * plane + col));
         }
-        if (a.has_prev && in_xy) hp = ldp(Hprev + (k * plane + j * a.nx + ia));
+        if (!kSlots && a.has_prev && in_xy) hp = ldp(Hprev + (k * plane + j * a.nx + ia));
         __syncthreads();
+        if constexpr (kSlots) {
+            const T* S = &Ps[(k - k0) & 1][0][2 * tid];
+            if (!wxa) uxa = S[0];
+            if (!wxb) uxb = S[1];
+            if (!wy) vy = ldp(S + 2 * kNT);
+            if (!zwall) wz = ldp(S + 4 * kNT);
+            if (a.has_prev && in_xy) hp = ldp(S + 6 * kNT);
+            if (ty == 0 && !wye) vye = ldp(S + 8 * kNT);
+            if (ty == 1 && tx < 4 && !wxe) {
+                uxe_a = S[8 * kNT];
+                uxe_b = S[8 * kNT + 1];
+            }
+        }
 
         const T(*P)[PX] = Cs[buf];
         const int cy = ty + kHalo, cx = 2 * tx + kHL2;  // smem position of cell ia
