@@ -287,11 +287,14 @@ def test_graph_replay_matches_direct_launches():
     ((400, 6, 6), (co.PERIODIC, co.NOFLUX, co.NOFLUX), "f32"),     # z 400 walls + update: cluster of 2
     ((6, 600, 7), (co.PERIODIC, co.PERIODIC, co.NOFLUX), "f32"),   # odd nx: shared-memory tile solver
     ((6, 300, 8), (co.PERIODIC, co.PERIODIC, co.NOFLUX), "f64"),   # FP64: one-column form
+    ((90, 100, 66), (co.PERIODIC, co.PERIODIC, co.NOFLUX), "f32"),  # y 100 periodic, z 90 walls + update: 8 warps x 16 rows, ragged
+    ((150, 200, 34), (co.PERIODIC, co.NOFLUX, co.PERIODIC), "f32"),  # y 200 walls, z 150 periodic + update: 16 warps x 16 rows
 ])
 def test_long_lines(shape, bc, prec):
     """Lines longer than 256 cells: up to 512, the cluster form of the
     two-column solver (FP32, even nx) or the one-column form; beyond, the tile
-    solver."""
+    solver.  Also ragged 65..256-cell lines on the 16-row shapes of the
+    two-column solver (8 or 16 warps, last warp partly past the line end)."""
     h = 1.0 / 64
     cn = 0.75 * h
     rng = np.random.default_rng(17)
