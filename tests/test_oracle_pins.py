@@ -327,3 +327,42 @@ def test_weno_linear_weights_exact_for_quartic():
         avg = (f(xf[1:]) - f(xf[:-1])) / hh
         errs.append(abs(co.weno5_reconstruct(*avg, 1e-6) - np.sin(3 * 0.3)))
     assert errs[0] / errs[1] > 24
+
+
+# ---------------------------------------------------------------------------
+# Temporal order of the whole step (RK3 with Crank-Nicolson and approximate
+# factorisation, Sec. 3 and Eqs. eq-fac-1..3): second order in dt
+# ---------------------------------------------------------------------------
+
+def _time_self_convergence(ns, T=0.5):
+    """Differences between solutions at time T with dt = T/n for successive
+    n, and the observed orders log2(e_i / e_{i+1}), on a smooth nonlinear
+    field of an 8^3 periodic box (psi'' > 0 everywhere, so the explicit term
+    is stable at every dt used)."""
+    n = 8
+    h = 1.0 / n
+    x = (np.arange(n) + 0.5) * h
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    C0 = 0.2 + 0.1 * np.cos(2 * np.pi * X) + 0.05 * np.sin(2 * np.pi * Y) * np.cos(2 * np.pi * Z)
+    sols = [co.step(C0, None, Params(n, n, n, h, cn=0.75 * h, pe=50.0, dt=T / m), m) for m in ns]
+    e = [np.linalg.norm(sols[i] - sols[i + 1]) for i in range(len(ns) - 1)]
+    return [np.log2(e[i] / e[i + 1]) for i in range(len(e) - 1)]
+
+
+def test_step_is_second_order_in_time():
+    orders = _time_self_convergence([4, 8, 16, 32, 64])
+    assert all(1.9 <= q <= 2.1 for q in orders[-2:]), orders
+
+
+def test_time_order_pin_detects_wrong_rk_coefficients(monkeypatch):
+    """Planted mistakes in the oracle's RK3 coefficient set fail the pin above:
+    a first-order set with the same sums, and an implicit weight alpha_3 off
+    by 2 % (the CN part then no longer sums to dt)."""
+    monkeypatch.setattr(co, "RK3_GAMMA", (1 / 3, 1 / 3, 1 / 3))
+    monkeypatch.setattr(co, "RK3_RHO", (0.0, 0.0, 0.0))
+    monkeypatch.setattr(co, "RK3_ALPHA", (1 / 3, 1 / 3, 1 / 3))
+    assert max(_time_self_convergence([4, 8, 16, 32, 64])[-2:]) < 1.2
+    monkeypatch.setattr(co, "RK3_GAMMA", (8 / 15, 5 / 12, 3 / 4))
+    monkeypatch.setattr(co, "RK3_RHO", (0.0, -17 / 60, -5 / 12))
+    monkeypatch.setattr(co, "RK3_ALPHA", (8 / 15, 2 / 15, 0.34))
+    assert _time_self_convergence([4, 8, 16, 32, 64])[-1] < 1.85
