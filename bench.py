@@ -83,6 +83,46 @@ def run_oracle(steps, warmup, sample=SAMPLE):
     return r["cells"], t
 
 
+_ORACLE_BATCH_SNIPPET = """
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import multiprocessing as mp
+from concurrent.futures import ProcessPoolExecutor
+import numpy as np
+from oracle import batch_timing as bt
+from paper_2105_01865_gb300 import inputs
+if __name__ == "__main__":
+    boxes = inputs.batch_boxes(64, 4, only=-1)
+    dts = json.loads(sys.stdin.read())
+    order = sorted(range(len(boxes)), key=lambda i: -int(np.prod(boxes[i]["shape"])))
+    n = len(os.sched_getaffinity(0))
+    with ProcessPoolExecutor(n, mp_context=mp.get_context("spawn")) as ex:
+        list(ex.map(bt.ready, [0.5] * n))
+        t0 = time.perf_counter()
+        res = list(ex.map(bt.box_step, order, [dts[i] for i in order]))
+        wall = time.perf_counter() - t0
+    print(json.dumps(dict(cells=sum(c for c, _ in res), wall=wall, cpu=sum(t for _, t in res), workers=n)))
+"""
+
+
+def run_oracle_batch(dts):
+    """The oracle on all 64 boxes of the batched workload (box i with step
+    dts[i]), one step each, over a spawn pool of one single-threaded oracle
+    process per available core."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = _ORACLE_BATCH_SNIPPET.format(root=ROOT)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT,
+                         input=json.dumps(list(dts)))
+    if out.returncode != 0:
+        raise RuntimeError("batched oracle leg failed:\n" + out.stderr[-2000:])
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    return dict(value=r["cells"] / r["wall"], unit="cell-updates/s", cores=r["workers"], kind="oracle",
+                single_core_value=r["cells"] / r["cpu"],
+                sample="all 64 boxes of the batched workload, one RK3 step each (FP64 numpy oracle), largest "
+                       "first over a spawn pool of one single-threaded oracle process per available core; "
+                       f"host CPU {cpu_model()}")
+
+
 def cpu_model():
     try:
         for line in open("/proc/cpuinfo"):
@@ -215,7 +255,8 @@ def batched_leg(args, dev, flush, rank=0, world=1):
     from paper_2105_01865_gb300.solver import Batch
     all_boxes = inputs.batch_boxes(64, seed=4)
     cells_all = [int(np.prod(b["shape"])) for b in all_boxes]
-    boxes = [all_boxes[i] for i in lpt_assign(cells_all, world)[rank]]
+    mine = lpt_assign(cells_all, world)[rank]
+    boxes = [all_boxes[i] for i in mine]
     for box in boxes:
         box["dt"] = 0.9 * stability.stable_dt(box["shape"], box["h"], box["bc"], box["cn"], box["pe"])
     cells = sum(cells_all)
@@ -242,6 +283,8 @@ def batched_leg(args, dev, flush, rank=0, world=1):
                              zchunk=sched[2], lpt=sched[3]),
                launches_per_step=b.launches_per_step(), autotune_candidates=report.count("\n") - 1)
     b.close()
+    # per-box steps for the CPU baseline of this workload (popped before printing)
+    out["_dts"] = {i: box["dt"] for i, box in zip(mine, boxes)}
     return out
 
 
@@ -513,6 +556,7 @@ def gpu_arm(args):
                h2d_bytes_per_step=ncell * 4, d2h_bytes_per_step=ncell * 4)
 
     batched = batched_leg(args, dev, flush, rank, world)
+    batch_dts = batched.pop("_dts")
     multires = multires_leg(args, dev, flush) if not args.no_multires else None
     schemes = scheme_leg(args, dev, W) if not args.no_scheme else None
     dirichlet = dirichlet_leg(args, dev, flush, W) if not args.no_scheme else None
@@ -536,6 +580,8 @@ def gpu_arm(args):
                 scheme_comparison=schemes, dirichlet_walls=dirichlet, clocks=clocks,
                 gpu_launches=args.steps * s32.launches_per_step())
     if rank == 0 and not args.no_cpu_baseline:
+        if world == 1:
+            batched["cpu_baseline"] = run_oracle_batch([batch_dts[i] for i in range(len(batch_dts))])
         cells, times = run_oracle(1, 0)
         cpu_v = cells * len(times) / sum(times)
         line["cpu_baseline"] = dict(value=cpu_v, unit="cell-updates/s", cores=1, kind="oracle",

@@ -217,10 +217,12 @@ def shear_drop_box(nx=256, ny=256, nz=128):
     return dict(shape=shape, h=h, bc=bc, cn=cn, pe=0.9 / cn, C=C, vel=vel)
 
 
-def batch_boxes(nbox=64, seed=4, sizes=(32, 48, 64, 96, 128)):
+def batch_boxes(nbox=64, seed=4, sizes=(32, 48, 64, 96, 128), only=None):
     """Independent periodic unit boxes of uneven size and parameters: n^3 with
     n ~ U{sizes}, h = 1/n, Cn ~ U[0.5 h, h], Pe log-uniform on [1e2, 1e4],
-    1..8 drops with R ~ U[0.08, 0.25] (non-overlapping, rejection sampled)."""
+    1..8 drops with R ~ U[0.08, 0.25] (non-overlapping, rejection sampled).
+    With only = i the random draws are the same but only box i's field is
+    built (the others carry C = None)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     boxes = []
     bc = (PERIODIC, PERIODIC, PERIODIC)
@@ -232,6 +234,6 @@ def batch_boxes(nbox=64, seed=4, sizes=(32, 48, 64, 96, 128)):
         ndrop = int(rng.integers(1, 9))
         centres, radii = random_drops(rng, ndrop, (1.0, 1.0, 1.0), 0.08, 0.25, 4 * cn, (False, False, False),
                                       max_tries=2000)
-        C = drops_field((n, n, n), h, bc, centres, radii, cn)
+        C = drops_field((n, n, n), h, bc, centres, radii, cn) if only is None or only == len(boxes) else None
         boxes.append(dict(shape=(n, n, n), h=h, bc=bc, cn=cn, pe=pe, C=C, vel=None))
     return boxes
