@@ -96,6 +96,8 @@ def test_fp64_advected_ragged(shape, bc):
     ((37, 11, 66), (co.NOFLUX, co.NOFLUX, co.PERIODIC)),     # several z chunks, periodic z faces
     ((6, 5, 6), (co.PERIODIC, co.NOFLUX, co.PERIODIC)),      # minimum even size
     ((9, 17, 33), (co.NOFLUX, co.PERIODIC, co.NOFLUX)),      # odd nx: one-cell-per-thread kernel
+    ((7, 9, 128), (co.PERIODIC, co.NOFLUX, co.NOFLUX)),      # 128-cell x-lines, odd line count
+    ((5, 7, 256), (co.PERIODIC, co.PERIODIC, co.NOFLUX)),    # 256-cell x-lines, odd line count
 ])
 def test_fp32_advected_ragged(shape, bc):
     """FP32 with walls, a random divergence-free flow and ragged tiles: every
