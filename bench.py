@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -162,10 +163,12 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, out_dir=None):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # raw samples: --clocks-dir if given, else a temporary directory
+        base = out_dir or os.path.join(tempfile.gettempdir(), "ch_bench_clocks")
+        self.path = os.path.join(base, f"clocks_rank{gpu_index}.csv")
 
     def __enter__(self):
         try:
@@ -494,7 +497,8 @@ def gpu_arm(args):
     # main FP32 line; nvidia-smi samples the clocks from here through the
     # batched and multi-resolution legs (all timed regions of this run)
     s32 = make("f32")
-    clk = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    clk = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local,
+                       args.clocks_dir)
     clk.__enter__()
     sec = timed(s32, args.steps, args.warmup)
     s32.sync()
@@ -603,6 +607,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clocks-dir", default=None, help="directory for the raw nvidia-smi clock samples")
     ap.add_argument("--no-multires", action="store_true", help="skip the 1024x1024x512 transfer + step leg")
     ap.add_argument("--no-scheme", action="store_true",
                     help="skip the split vs standard scheme comparison and the Dirichlet-wall leg")

@@ -16,7 +16,7 @@ It follows "An efficient phase-field method for turbulent multiphase flows"
 * Sec. 3.1, Eqs. (eq-re), (eq-fac), (eq-fac-1..3): Crank-Nicolson in delta
   form, approximately factorised into an x-, a y- and a z-line solve.
 
-Readings where the paper is silent (all listed in the design doc):
+Readings where the paper is silent:
 * RK3 coefficients (gamma, rho) = (8/15, 0), (5/12, -17/60), (3/4, -5/12) and
   the per-substep Crank-Nicolson step alpha_l*dt, alpha_l = gamma_l + rho_l
   (the low-storage scheme the paper cites for Sec. 3).

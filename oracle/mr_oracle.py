@@ -23,7 +23,7 @@ the fine cell centres, queries at the coarse cell centres), applied to C and
 to the fine surface-tension force, from which the coarse density and
 viscosity follow (Eqs. eq-rho, eq-mu, eq-fst).
 
-Readings (listed in the design doc): the cubic Hermite segment on [x_j, x_{j+1}]
+Readings where the paper is silent: the cubic Hermite segment on [x_j, x_{j+1}]
 takes node slopes from central differences over the neighbouring nodes
 (non-uniform Catmull-Rom); the base node is the last node at or left of the
 query point; walled directions clamp the stencil into the node range and use

@@ -192,8 +192,8 @@ def random_drops(rng, n, box, rmin, rmax, gap, walls, max_tries=200000):
 
 
 # ---------------------------------------------------------------------------
-# Workloads (fields only; time step and physical constants are chosen by the
-# caller, see the design doc for the recipe)
+# Workloads (fields only; the caller chooses the time step and the physical
+# constants)
 # ---------------------------------------------------------------------------
 
 def single_drop_box(n=64):
