@@ -366,3 +366,26 @@ def test_time_order_pin_detects_wrong_rk_coefficients(monkeypatch):
     monkeypatch.setattr(co, "RK3_RHO", (0.0, -17 / 60, -5 / 12))
     monkeypatch.setattr(co, "RK3_ALPHA", (8 / 15, 2 / 15, 0.34))
     assert _time_self_convergence([4, 8, 16, 32, 64])[-1] < 1.85
+
+
+# ---------------------------------------------------------------------------
+# Spatial order of the whole step (Sec. 3: second-order central differences,
+# the pentadiagonal A_d, WENO5 advection): second order in h at fixed Cn
+# ---------------------------------------------------------------------------
+
+def test_step_is_second_order_in_space():
+    """Self-convergence of a smooth x-dependent field advected at u = 0.5 to
+    T = 0.02 on 32, 64 and 128 cells (Cn = 0.05 fixed, dt = 1e-4 so the time
+    error is negligible): the coarse solution against the mean of the two fine
+    cells that share its centre."""
+    def solve(n, T=0.02, dt=1e-4):
+        h = 1.0 / n
+        x = (np.arange(n) + 0.5) * h
+        prof = 0.3 + 0.2 * np.sin(2 * np.pi * x) + 0.1 * np.cos(4 * np.pi * x)
+        C0 = np.broadcast_to(prof[None, None, :], (4, 4, n)).copy()
+        vel = (np.full((4, 4, n), 0.5), np.zeros((4, 4, n)), np.zeros((4, 4, n)))
+        return co.step(C0, vel, Params(n, 4, 4, h, cn=0.05, pe=10.0, dt=dt), int(round(T / dt)))[0, 0]
+    s = [solve(n) for n in (32, 64, 128)]
+    e = [np.abs(s[i] - 0.5 * (s[i + 1][0::2] + s[i + 1][1::2])).max() for i in range(2)]
+    order = np.log2(e[0] / e[1])
+    assert 1.9 <= order <= 2.1, (e, order)
