@@ -213,6 +213,9 @@ class ClockSampler:
         return dict(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax), reasons=sorted(reasons), samples=len(sm))
 
 
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal (data sheet); the measured copy peak is the roofline's denominator
+
+
 def measured_peak_hbm():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -534,9 +537,11 @@ def gpu_arm(args):
                     frac=achieved / peak_fp32, traffic=traffic.get(names[0]),
                     peak_source=f"derived: 152 SMs x 128 FP32 lanes x 2 flops x {sm_mhz:.0f} MHz",
                     kernels={n: dict(ms=m, algo_bytes_per_cell=b, gbs=b * ncell / (m * 1e-3) / 1e9,
-                                     hbm_frac=b * ncell / (m * 1e-3) / 1e9 / peak_hbm, traffic=traffic.get(n))
+                                     hbm_frac=b * ncell / (m * 1e-3) / 1e9 / peak_hbm,
+                                     hbm_frac_nominal=b * ncell / (m * 1e-3) / 1e9 / NOMINAL_HBM_GBS,
+                                     traffic=traffic.get(n))
                              for n, m, b in zip(names, kms, kbytes)},
-                    hbm_peak=dict(value=peak_hbm, unit="GB/s", source=peak_src))
+                    hbm_peak=dict(value=peak_hbm, unit="GB/s", source=peak_src, nominal=NOMINAL_HBM_GBS))
 
     # end to end through the public API with host buffers: pinned H2D of C,
     # one step, D2H of C, every step
