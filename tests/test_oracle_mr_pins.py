@@ -33,7 +33,7 @@ def test_linear_exact_on_stretched_walled_grid_incl_ends():
     vals = 2.5 * nodes - 0.7
     xq = np.linspace(0.0, 1.0, 53)                   # includes extrapolated end segments
     got = np.array([mo.interp_1d(vals, nodes, x, NOFLUX, 1.0) for x in xq])
-    np.testing.assert_allclose(got, 2.5 * xq - 0.7, atol=1e-13)
+    np.testing.assert_allclose(got, 2.5 * xq - 0.7, rtol=0, atol=1e-13)
 
 
 def test_quadratic_exact_on_uniform_interior():
@@ -41,7 +41,7 @@ def test_quadratic_exact_on_uniform_interior():
     vals = 3 * nodes ** 2 - nodes + 0.2
     xq = np.linspace(nodes[1], nodes[-2], 31)
     got = np.array([mo.interp_1d(vals, nodes, x, NOFLUX, 1.0) for x in xq])
-    np.testing.assert_allclose(got, 3 * xq ** 2 - xq + 0.2, atol=1e-13)
+    np.testing.assert_allclose(got, 3 * xq ** 2 - xq + 0.2, rtol=0, atol=1e-13)
 
 
 def test_periodic_wrap_and_order():
@@ -60,7 +60,7 @@ def test_tables_identity_and_partition_of_unity(bc):
     n = 12
     faces = inputs.uniform_faces(n, 1.0)
     starts, w = mo.tables(faces, faces, faces, (n, n, n), 1.0 / n, (bc, bc, bc))[0]
-    np.testing.assert_allclose(w.sum(1), 1.0, atol=1e-14)
+    np.testing.assert_allclose(w.sum(1), 1.0, rtol=0, atol=1e-14)
     # fine centres coincide with coarse centres -> each weight row is a unit vector on the node itself
     for i in range(n):
         pos = [(starts[i] + m) % n for m in range(4)]
@@ -115,5 +115,5 @@ def test_linear_shear_transfers_exactly():
     h = 1.0 / 8
     (u, v, w), _ = mo.transfer(uc, vc, wc, xf, yf, zf, fine_n, h, bc)
     zfine = (np.arange(8) + 0.5) * h
-    np.testing.assert_allclose(u, np.broadcast_to((zfine - 0.5)[:, None, None], u.shape), atol=1e-14)
+    np.testing.assert_allclose(u, np.broadcast_to((zfine - 0.5)[:, None, None], u.shape), rtol=0, atol=1e-14)
     assert np.abs(v).max() < 1e-14 and np.abs(w).max() < 1e-14

@@ -165,7 +165,7 @@ def test_linear_mode_matches_closed_form(C0, m):
     nsteps = 5
     out = co.step(C, None, p, nsteps, psi_p=lambda c: psi2 * (c - C0))
     g = closed_form_gain(k, p, psi2)
-    np.testing.assert_allclose(out - C0, eps * g ** nsteps * mode, atol=1e-13 * eps * max(1, abs(g) ** nsteps))
+    np.testing.assert_allclose(out - C0, eps * g ** nsteps * mode, rtol=0, atol=1e-13 * eps * max(1, abs(g) ** nsteps))
 
 
 # ---------------------------------------------------------------------------
@@ -199,7 +199,7 @@ def test_line_solves_match_dense_kronecker():
     I = np.eye(N)
     prod = (I + c * dense[0]) @ (I + c * dense[1]) @ (I + c * dense[2])
     cross = c ** 2 * (dense[0] @ dense[1] + dense[0] @ dense[2] + dense[1] @ dense[2]) + c ** 3 * dense[0] @ dense[1] @ dense[2]
-    np.testing.assert_allclose(prod, I + c * sum(dense) + cross, atol=1e-9 * np.abs(prod).max())
+    np.testing.assert_allclose(prod, I + c * sum(dense) + cross, rtol=0, atol=1e-9 * np.abs(prod).max())
 
 
 # ---------------------------------------------------------------------------
@@ -236,7 +236,7 @@ def test_free_stream_preserved():
     p = Params(10, 9, 8, h, cn=0.07, pe=10.0, dt=0.02, bc=bc)
     C = np.full(shape, 0.3)
     C1 = co.step(C, vel, p, 5)
-    np.testing.assert_allclose(C1, 0.3, atol=1e-13)
+    np.testing.assert_allclose(C1, 0.3, rtol=0, atol=1e-13)
 
 
 def test_free_energy_decays_without_flow():
@@ -389,3 +389,47 @@ def test_step_is_second_order_in_space():
     e = [np.abs(s[i] - 0.5 * (s[i + 1][0::2] + s[i + 1][1::2])).max() for i in range(2)]
     order = np.log2(e[0] / e[1])
     assert 1.9 <= order <= 2.1, (e, order)
+
+
+def test_weno_matches_the_integral_definition_of_smoothness():
+    """WENO5-JS from its definition (Jiang and Shu 1996): the three quadratics
+    with the stencils' cell averages, evaluated at the face; smoothness
+    indicators beta_k = sum_{l=1,2} h^{2l-1} int_cell (d^l p_k/dx^l)^2 over the
+    upwind cell; weights d_k / (eps + beta_k)^2 with d = (1/10, 6/10, 3/10).
+    Random (non-smooth) data, so the nonlinear weights matter."""
+    def from_definition(v, eps):
+        vals, betas = [], []
+        for cells in ([-2, -1, 0], [-1, 0, 1], [0, 1, 2]):      # cell 0 holds v3; the face is at x = 1/2 (h = 1)
+            A = np.array([[1.0, j, j * j + 1.0 / 12.0] for j in cells])   # averages of 1, x, x^2 over cell j
+            c0, c1, c2 = np.linalg.solve(A, np.array([v[j + 2] for j in cells]))
+            vals.append(c0 + c1 / 2 + c2 / 4)
+            betas.append(c1 ** 2 + c2 ** 2 / 3 + 4 * c2 ** 2)   # int_{-1/2}^{1/2} p'^2 + p''^2
+        a = [dk / (eps + b) ** 2 for dk, b in zip((0.1, 0.6, 0.3), betas)]
+        return sum(ai * q for ai, q in zip(a, vals)) / sum(a)
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        v = rng.standard_normal(5)
+        got = co.weno5_reconstruct(*[np.float64(t) for t in v], 1e-6)
+        assert abs(got - from_definition(v, 1e-6)) <= 1e-13 * max(1.0, abs(got))
+
+
+# ---------------------------------------------------------------------------
+# Free energy of a planar interface: 2 sigma A with sigma = sqrt(2) Cn / 12,
+# the surface energy of the equilibrium profile C = (1 + tanh(x / (2 sqrt(2) Cn))) / 2
+# of psi = C^2 (C - 1)^2 / 4 with gradient coefficient Cn^2
+# ---------------------------------------------------------------------------
+
+def test_free_energy_of_a_planar_interface():
+    cn = 0.02
+    sigma = np.sqrt(2.0) * cn / 12.0
+    errs = []
+    for n in (64, 128):
+        h = 1.0 / n
+        x = (np.arange(n) + 0.5) * h
+        w = 2.0 * np.sqrt(2.0) * cn
+        prof = 0.5 * (np.tanh((x - 0.25) / w) - np.tanh((x - 0.75) / w))   # two interfaces, periodic
+        C = np.broadcast_to(prof[None, None, :], (4, 4, n)).copy()
+        F = co.free_energy(C, Params(n, 4, 4, h, cn=cn, pe=1.0, dt=1.0))
+        errs.append(F / (2.0 * sigma * (4 * h) ** 2) - 1.0)
+    assert abs(errs[1]) < 1e-3
+    assert 3.5 < errs[0] / errs[1] < 4.5        # second order in h

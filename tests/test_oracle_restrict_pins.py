@@ -63,8 +63,8 @@ def test_quadratics_are_exact_away_from_clamped_ends():
 
 def test_density_and_viscosity_definitions():
     C = np.array([0.0, 1.0, 0.5, 0.25])
-    np.testing.assert_allclose(co.density(C, 0.1), [0.1, 1.0, 0.55, 0.325])
-    np.testing.assert_allclose(co.viscosity(C, 2.0), [2.0, 1.0, 1.5, 1.75])
+    np.testing.assert_allclose(co.density(C, 0.1), [0.1, 1.0, 0.55, 0.325], rtol=1e-15)
+    np.testing.assert_allclose(co.viscosity(C, 2.0), [2.0, 1.0, 1.5, 1.75], rtol=1e-15)
 
 
 def test_surface_tension_converges_to_the_continuum_force():
