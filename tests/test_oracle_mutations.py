@@ -41,7 +41,9 @@ ADJ = _load("test_oracle_adjoint_pins")
 
 _orig = dict(apply_A=co.apply_A, line_solve=co.line_solve, lap_h=co.lap_h, face_fluxes=co.face_fluxes,
              pad=co.pad, hermite_segment=mo.hermite_segment, biharmonic_h=co.biharmonic_h,
-             density=co.density, free_energy=co.free_energy)
+             density=co.density, free_energy=co.free_energy, coarse_gradients=mo.coarse_gradients,
+             interp_plane=mo.interp_plane, surface_tension=co.surface_tension,
+             restriction_tables=mo.restriction_tables)
 
 
 def rk3_rho_sign(mp):
@@ -167,6 +169,26 @@ def energy_gradient_weight(mp):
         _orig["free_energy"](C, p) - p.h ** 3 * float(np.sum(co.psi(C)))))
 
 
+def transfer_gradient_scale(mp):
+    def grads(*a):
+        gx, gy, gz = _orig["coarse_gradients"](*a)
+        return 1.01 * gx, gy, gz
+    mp.setattr(mo, "coarse_gradients", grads)
+
+
+def transfer_reference_plane(mp):
+    mp.setattr(mo, "interp_plane", lambda P, r, c: 0.9 * _orig["interp_plane"](P, r, c))
+
+
+def surface_tension_coefficient(mp):
+    mp.setattr(co, "surface_tension", lambda C, p: tuple(1.05 * f for f in _orig["surface_tension"](C, p)))
+
+
+def restriction_weights(mp):
+    mp.setattr(mo, "restriction_tables",
+               lambda *a: [(s, 1.01 * w) for s, w in _orig["restriction_tables"](*a)])
+
+
 # mistake -> the pins that must catch it (at least one fails)
 CASES = {
     "rk3_rho_sign": (rk3_rho_sign, [lambda: PINS.test_linear_mode_matches_closed_form(0.5, (1, 0, 0)),
@@ -194,6 +216,14 @@ CASES = {
     "density_phases_swapped": (density_phases_swapped, [RS.test_density_and_viscosity_definitions]),
     "adjoint_psi_pp": (adjoint_psi_pp, [lambda: ADJ.test_adjoint_transposes_complex_step_jvp((PERIODIC,) * 3)]),
     "energy_gradient_weight": (energy_gradient_weight, [PINS.test_free_energy_of_a_planar_interface]),
+    "standard_rk3_rho_dropped": (dropped_h_prev, [lambda: STD.test_rk3_step_of_a_linear_mode_matches_closed_form(0.5)]),
+    "transfer_gradient_scale": (transfer_gradient_scale,
+                                [lambda: MR.test_fine_field_solenoidal((PERIODIC, PERIODIC, NOFLUX))]),
+    "transfer_reference_plane": (transfer_reference_plane, [MR.test_linear_shear_transfers_exactly]),
+    "surface_tension_coefficient": (surface_tension_coefficient,
+                                    [RS.test_surface_tension_converges_to_the_continuum_force]),
+    "restriction_weights": (restriction_weights,
+                            [lambda: RS.test_coincident_meshes_give_the_identity((PERIODIC, PERIODIC, NOFLUX))]),
 }
 
 
