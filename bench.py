@@ -1,12 +1,18 @@
-"""Throughput of the Cahn-Hilliard fine-grid step on GB300.
+"""Throughput of the Cahn-Hilliard hot path on GB300.
 
-Workload (default): drop in imposed shear on a 256 x 256 x 128 uniform mesh,
-x/y periodic on [0, 2], no-flux walls at z = 0, 1, u = (z - 1/2, 0, 0),
-Cn = 0.75 h, Pe = 0.9 / Cn, FP32 fields (the precision form), dt =
-min(0.9 dt_stab, CFL 0.5).  One step = one full RK3 step (three substeps of
-explicit RHS + x, y, z line solves) over every cell.  Metric: fine-grid
-cell-updates/s.  The working set (C, two H, rhs, three face velocities,
-~235 MB) exceeds the 129 MB L2, and L2 is also flushed between timed steps.
+Headline workload: the multiple-resolution case, the largest configuration
+that fits one GPU.  A coarse 256 x 256 x 128 mesh, tanh-stretched in z
+(walls at z = 0, 1; x, y periodic on [0, 2]), carries a seeded
+divergence-free random-Fourier face velocity; it is transferred to the
+uniform 1024 x 1024 x 512 fine mesh (h = 1/512, 5.37e8 cells) of the volume
+fraction C, which holds ~1000 drops of radius U[0.01, 0.03]; Cn = 0.75 h,
+Pe = 0.9 / Cn, FP32 fields with FP64 reductions, dt = min(0.9 dt_stab, CFL
+0.5).  One step is one pass of the whole hot path: the coarse velocity handed
+in, the velocity transfer (normal gradients, Hermite interpolation,
+integration), one full RK3 step (three substeps of explicit right-hand side
+and x, y, z line solves), and the FP64 mass and free energy.  Metric:
+fine-grid cell-updates/s.  The working set (~15 GB) exceeds the 129 MB L2,
+which is also flushed between timed steps.
 
 ``python bench.py [--gpus N --steps K --warmup W]`` prints one JSON line.
 ``--impl reference`` times the CPU FP64 oracle instead (the slow baseline).
@@ -30,58 +36,105 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(name="shear_drop_256x256x128", nx=256, ny=256, nz=128)
-# CPU sample for the oracle legs: the same workload recipe on a 128 x 128 x 64 mesh
-SAMPLE = dict(nx=128, ny=128, nz=64)
+HEADLINE = dict(name="multires_1024x1024x512_from_256x256x128", fine=(1024, 1024, 512), coarse=(256, 256, 128),
+                ndrops=1000)
+# CPU sample of the headline workload for the oracle legs: the same recipe on
+# a 128 x 128 x 64 fine mesh over a 32 x 32 x 16 coarse one (50 drops)
+SAMPLE = dict(fine=(128, 128, 64), coarse=(32, 32, 16), ndrops=50)
+SHEAR = dict(name="shear_drop_256x256x128", nx=256, ny=256, nz=128)
 METRIC = "fine-grid CH cell-updates/s"
 L2_FLUSH_BYTES = 256 << 20
+# kernel launches of one hot-path step besides ch_step's own: 4 transfer
+# kernels, 2 for the mass and 2 for the free-energy reduction
+LAUNCHES_AROUND_STEP = 4 + 2 + 2
 
 
 def _rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
-def workload_inputs(nx, ny, nz):
+def multires_inputs(fine, coarse, ndrops):
     from paper_2105_01865_gb300 import inputs, stability
-    f = inputs.shear_drop_box(nx, ny, nz)
+    f = inputs.multires_box(tuple(fine), tuple(coarse), ndrops)
     h = f["h"]
-    dt = min(0.9 * stability.stable_dt(f["shape"], h, f["bc"], f["cn"], f["pe"]), 0.5 * h / 0.5)
-    f["dt"] = dt
+    f["dt"] = min(0.9 * stability.stable_dt(f["shape"], h, f["bc"], f["cn"], f["pe"]), 0.5 * h / 1.0)
     return f
 
 
+def shear_inputs(nx, ny, nz):
+    from paper_2105_01865_gb300 import inputs, stability
+    f = inputs.shear_drop_box(nx, ny, nz)
+    h = f["h"]
+    f["dt"] = min(0.9 * stability.stable_dt(f["shape"], h, f["bc"], f["cn"], f["pe"]), 0.5 * h / 0.5)
+    return f
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 # ---------------------------------------------------------------------------
-# oracle (CPU) legs, run in a fresh single-threaded interpreter
+# oracle (CPU) legs, run in fresh single-threaded interpreters
 # ---------------------------------------------------------------------------
 
-_ORACLE_SNIPPET = r"""
-import json, sys, time
+_ENV1 = dict(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+
+_ORACLE_MR_SNIPPET = """
+import json, os, sys, time
 sys.path.insert(0, {root!r})
-import numpy as np
-from oracle import ch_oracle as co
-import bench
-f = bench.workload_inputs({nx}, {ny}, {nz})
-nz, ny, nx = f["shape"]
-p = co.Params(nx, ny, nz, f["h"], cn=f["cn"], pe=f["pe"], dt=f["dt"], bc=f["bc"])
-C = f["C"]
-times = []
-for s in range({total}):
-    t0 = time.perf_counter()
-    C = co.step(C, f["vel"], p, 1)
-    times.append(time.perf_counter() - t0)
-print(json.dumps(dict(times=times, cells=nx * ny * nz)))
+import multiprocessing as mp
+from concurrent.futures import ProcessPoolExecutor
+from oracle import batch_timing as bt
+if __name__ == "__main__":
+    a = json.loads(sys.stdin.read())
+    fine, coarse, ndrops, dt = a["fine"], a["coarse"], a["ndrops"], a["dt"]
+    out = dict()
+    if a["single"]:
+        # single thread, this process: warm-up steps, then the timed steps
+        times = [bt.multires_step(fine, coarse, ndrops, dt)[1] for _ in range(a["warmup"] + a["steps"])]
+        cells = fine[0] * fine[1] * fine[2]
+        out["single"] = dict(cells=cells, times=times[a["warmup"]:])
+    if a["pool"]:
+        # all cores: one single-threaded oracle process per available core, each
+        # running one step of the same sample after a warm-up step of its own
+        n = len(os.sched_getaffinity(0))
+        with ProcessPoolExecutor(n, mp_context=mp.get_context("spawn")) as ex:
+            list(ex.map(bt.multires_step, [fine] * n, [coarse] * n, [ndrops] * n, [dt] * n))
+            t0 = time.perf_counter()
+            res = list(ex.map(bt.multires_step, [fine] * n, [coarse] * n, [ndrops] * n, [dt] * n))
+            wall = time.perf_counter() - t0
+        out["pool"] = dict(cells=sum(c for c, _ in res), wall=wall, workers=n)
+    print(json.dumps(out))
 """
 
 
-def run_oracle(steps, warmup, sample=SAMPLE):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = _ORACLE_SNIPPET.format(root=ROOT, total=steps + warmup, **sample)
-    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT)
+def run_oracle_multires(steps, warmup, single=True, pool=True, sample=SAMPLE):
+    """The oracle's hot-path step (transfer, RK3 step, mass, free energy) on the
+    CPU sample of the headline workload: `steps` timed single-threaded steps
+    after `warmup`, and/or one step in every process of an all-cores pool."""
+    f = multires_inputs(sample["fine"], sample["coarse"], sample["ndrops"])
+    env = dict(os.environ, **_ENV1)
+    arg = dict(fine=list(sample["fine"]), coarse=list(sample["coarse"]), ndrops=sample["ndrops"], dt=f["dt"],
+               steps=steps, warmup=warmup, single=single, pool=pool)
+    out = subprocess.run([sys.executable, "-c", _ORACLE_MR_SNIPPET.format(root=ROOT)], capture_output=True,
+                         text=True, env=env, cwd=ROOT, input=json.dumps(arg))
     if out.returncode != 0:
         raise RuntimeError("oracle leg failed:\n" + out.stderr[-2000:])
-    r = json.loads(out.stdout.strip().splitlines()[-1])
-    t = r["times"][warmup:]
-    return r["cells"], t
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def sample_text(extra=""):
+    fx, fy, fz = SAMPLE["fine"]
+    cx, cy, cz = SAMPLE["coarse"]
+    return (f"FP64 numpy oracle, one hot-path step (velocity transfer, RK3 step, mass, free energy) of the "
+            f"multiple-resolution recipe on a {fx}x{fy}x{fz} fine mesh over a {cx}x{cy}x{cz} stretched coarse "
+            f"mesh ({SAMPLE['ndrops']} drops){extra}; host CPU {cpu_model()}")
 
 
 _ORACLE_BATCH_SNIPPET = """
@@ -110,7 +163,7 @@ def run_oracle_batch(dts):
     """The oracle on all 64 boxes of the batched workload (box i with step
     dts[i]), one step each, over a spawn pool of one single-threaded oracle
     process per available core."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    env = dict(os.environ, **_ENV1)
     code = _ORACLE_BATCH_SNIPPET.format(root=ROOT)
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT,
                          input=json.dumps(list(dts)))
@@ -124,31 +177,19 @@ def run_oracle_batch(dts):
                        f"host CPU {cpu_model()}")
 
 
-def cpu_model():
-    try:
-        for line in open("/proc/cpuinfo"):
-            if line.lower().startswith(("model name", "cpu part")):
-                return line.split(":", 1)[1].strip()
-    except OSError:
-        pass
-    return "unknown"
-
-
 def reference_arm(args):
     rank, world, _ = _rank()
     if rank != 0:
         return
-    cells, times = run_oracle(args.steps, args.warmup)
-    sec = sum(times)
-    value = cells * len(times) / sec
+    r = run_oracle_multires(args.steps, args.warmup, single=True, pool=False)["single"]
+    sec = sum(r["times"])
+    value = r["cells"] * len(r["times"]) / sec
     line = dict(metric=METRIC, value=value, unit="cell-updates/s", n_gpus=args.gpus, steps=args.steps,
-                warmup=args.warmup, ms_per_step=1e3 * sec / len(times), higher_is_better=True, scaling="weak",
+                warmup=args.warmup, ms_per_step=1e3 * sec / len(r["times"]), higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
-                config=dict(workload=WORKLOAD["name"], global_batch=1, seq_len=0, parallelism="replicas"),
+                config=dict(workload=HEADLINE["name"], global_batch=1, seq_len=0, parallelism="replicas"),
                 cpu_baseline=dict(value=value, unit="cell-updates/s", cores=1, kind="oracle",
-                                  sample=f"FP64 numpy oracle, one RK3 step per timed step of the same shear-drop "
-                                         f"recipe on a {SAMPLE['nx']}x{SAMPLE['ny']}x{SAMPLE['nz']} mesh, "
-                                         f"single thread, host CPU {cpu_model()}"),
+                                  sample=sample_text(", one step per timed step, single thread")),
                 e2e=dict(value=value, unit="cell-updates/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0),
                 gpu_launches=0)
     print(json.dumps(line), flush=True)
@@ -214,6 +255,21 @@ class ClockSampler:
 
 
 NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal (data sheet); the measured copy peak is the roofline's denominator
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+PEAK_FP32_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12  # FFMA per lane per clock, 2 flops
+# Algorithmic FP32 flops per cell of one explicit right-hand-side launch with
+# advection (the itemised count of the kernel's arithmetic, minimal form):
+# 3 WENO5 faces x 69 (3 candidates 15, 3 smoothness indicators 33, 3 weights
+# 12, normalised combination 8, flux 1) = 207; divergence 6; psi' 4; 7-point
+# Laplacian 9; M lap psi' + advection 2; the three fourth differences A_d C
+# and their scaled sum 24; RK/CN combination 5 (4 without H^{l-1}).
+EXPLICIT_FLOPS_PER_CELL = 257.0
+# Algorithmic bytes per cell of one launch (FP32): explicit = C + u + v + w
+# read, H + r written (24 B), + H^{l-1} read on substeps 2 and 3 (28 B), mean
+# 80/3; x and y solves 8 B; z solve + update 12 B.
+STEP_KERNELS = ["ch_explicit_rhs", "ch_solve_x", "ch_solve_y", "ch_solve_z_update"]
+STEP_BYTES = [80.0 / 3.0, 8.0, 8.0, 12.0]
+INTERP_KERNELS = ["mr_gradients", "mr_integrate_x", "mr_integrate_y", "mr_integrate_z"]
 
 
 def measured_peak_hbm():
@@ -240,15 +296,16 @@ def kernel_source_sha():
 
 
 def recorded_traffic():
-    """DRAM bytes per launch (ncu dram__bytes_read + write) recorded in
-    profiles/ncu_traffic.json, only if it was taken on the current kernels."""
+    """DRAM bytes per cell of one launch (ncu dram__bytes_read + write divided
+    by the cells of the captured case) recorded in profiles/ncu_traffic.json,
+    only if it was taken on the current kernels."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
     except (OSError, ValueError):
         return {}
     if rec.get("source_sha") != kernel_source_sha():
         return {}
-    return rec.get("bytes_per_launch", {})
+    return rec.get("bytes_per_cell", {})
 
 
 def batched_leg(args, dev, flush, rank=0, world=1):
@@ -271,7 +328,8 @@ def batched_leg(args, dev, flush, rank=0, world=1):
     st = b.stream
     for _ in range(args.warmup):
         b.step(1)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    k = max(3, min(args.steps, 20))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
     torch.cuda.synchronize(dev)
     with torch.cuda.stream(st):
         for a, c in ev:
@@ -283,87 +341,93 @@ def batched_leg(args, dev, flush, rank=0, world=1):
     b.sync()
     sec = max_over_ranks(sum(a.elapsed_time(c) for a, c in ev) / 1e3)
     sched = b.schedule()
-    out = dict(value=cells * args.steps / sec, unit="cell-updates/s", ms_per_step=1e3 * sec / args.steps,
+    peak_hbm, _ = measured_peak_hbm()
+    out = dict(value=cells * k / sec, unit="cell-updates/s", ms_per_step=1e3 * sec / k, steps=k,
                boxes=len(all_boxes), cells=cells, dtype="f32", placement="LPT on cell counts, no collective",
                schedule=dict(mode="persistent" if sched[0] == 0 else "phased", blocks_per_sm=sched[1],
                              zchunk=sched[2], lpt=sched[3]),
-               launches_per_step=b.launches_per_step(), autotune_candidates=report.count("\n") - 1)
+               launches_per_step=b.launches_per_step(), autotune_candidates=report.count("\n") - 1,
+               hbm_frac=128.0 * cells / (sec / k) / 1e9 / peak_hbm)
     b.close()
     # per-box steps for the CPU baseline of this workload (popped before printing)
     out["_dts"] = {i: box["dt"] for i, box in zip(mine, boxes)}
     return out
 
 
-def multires_leg(args, dev, flush):
-    """Multiple-resolution workload: seeded divergence-free coarse velocity on
-    a 256 x 256 x 128 mesh (tanh-stretched z, walls at z = 0, 1) transferred
-    to the 1024 x 1024 x 512 uniform FP32 fine mesh holding ~1000 drops of
-    radius U[0.01, 0.03]; times the transfer, the down-sampling of C (with
-    rho, mu, F_st on the coarse mesh) and the fine CH step."""
+def shear_leg(args, dev, flush):
+    """The drop in imposed shear, 256 x 256 x 128 (x, y periodic on [0, 2],
+    no-flux walls at z = 0, 1, u = (z - 1/2, 0, 0)), FP32: the step alone
+    (u is prescribed, no transfer), L2 flushed between steps, with per-kernel
+    durations and HBM fractions; the plain FP64 step on the same box."""
     import torch
-    from paper_2105_01865_gb300 import inputs, stability
+    from paper_2105_01865_gb300 import capi
     from paper_2105_01865_gb300.solver import Solver
-    nx, ny, nz = 1024, 1024, 512
-    h = 1.0 / nz
-    bc = (0, 0, 1)
-    cn = 0.75 * h
-    pe = 0.9 / cn
-    xf, yf = inputs.uniform_faces(256, 2.0), inputs.uniform_faces(256, 2.0)
-    zf = inputs.stretched_faces(128, 1.0, 2.0)
-    uc, vc, wc = inputs.curl_velocity(xf, yf, zf, bc, 3, kmax=8)
-    rng = np.random.Generator(np.random.PCG64(3))
-    centres, radii = inputs.random_drops(rng, 1000, (2.0, 2.0, 1.0), 0.01, 0.03, 4 * cn, (True, True, True))
-    C0 = inputs.drops_field_local((nz, ny, nx), h, centres, radii, cn, 8 * cn)
-    dt = min(0.9 * stability.stable_dt((nz, ny, nx), h, bc, cn, pe), 0.5 * h / 1.0)
-    s = Solver((nz, ny, nx), h, bc, cn, pe, dt, C0, precision="f32", coarse_faces=(xf, yf, zf), device=dev)
-    s.set_velocity_coarse(uc, vc, wc)
-    st = s.stream
-
-    def timed(fn, reps):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    W = SHEAR
+    f = shear_inputs(W["nx"], W["ny"], W["nz"])
+    ncell = W["nx"] * W["ny"] * W["nz"]
+    out = {}
+    for prec in ("f32", "f64"):
+        s = Solver(f["shape"], f["h"], f["bc"], f["cn"], f["pe"], f["dt"], f["C"], precision=prec, advect=True,
+                   device=dev)
+        s.set_velocity_fine(*f["vel"])
+        k = max(3, min(args.steps, 20)) if prec == "f32" else 5
+        for _ in range(3):
+            s.step(1)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
         torch.cuda.synchronize(dev)
-        with torch.cuda.stream(st):
-            for a, c in ev:
+        with torch.cuda.stream(s.stream):
+            for a, b in ev:
                 flush.fill_(1)
-                a.record(st)
-                fn()
-                c.record(st)
+                a.record(s.stream)
+                s.step(1)
+                b.record(s.stream)
         torch.cuda.synchronize(dev)
-        return sum(a.elapsed_time(c) for a, c in ev) / reps
-
-    s.interp_to_fine()
-    interp_ms = timed(s.interp_to_fine, 3)
-    # down-sampling back-coupling: coarse C, rho, mu and F_st (Sec. 3.4)
-    s.restrict_to_coarse(0.05, 1.0)
-    restrict_ms = timed(lambda: s.restrict_to_coarse(0.05, 1.0), 3)
-    for _ in range(3):
-        s.step(1)
-    k = max(3, min(args.steps, 20))
-    step_ms = timed(lambda: s.step(1), k)
-    s.sync()
-    cells = nx * ny * nz
-    out = dict(value=cells / (step_ms * 1e-3), unit="cell-updates/s", step_ms=step_ms, interp_ms=interp_ms,
-               cells=cells, coarse_cells=256 * 256 * 128, drops=len(radii), steps=k, dtype="f32",
-               interp_fine_faces_gbs=3 * cells * 4 / (interp_ms * 1e-3) / 1e9,
-               restrict_ms=restrict_ms,
-               restrict_fine_read_gbs=cells * 4 / (restrict_ms * 1e-3) / 1e9)
-    s.close()
-    return out
+        ms = sum(a.elapsed_time(b) for a, b in ev) / k
+        out[prec] = dict(ms_per_step=ms, value=ncell / (ms * 1e-3), steps=k)
+        if prec == "f32":
+            kms = kernel_means(s, flush, dev, 10)
+            peak_hbm, _ = measured_peak_hbm()
+            out["kernels"] = {n: dict(ms=m, gbs=b * ncell / (m * 1e-3) / 1e9,
+                                      hbm_frac=b * ncell / (m * 1e-3) / 1e9 / peak_hbm)
+                              for n, m, b in zip(STEP_KERNELS, kms, STEP_BYTES)}
+            out["explicit_tflops"] = EXPLICIT_FLOPS_PER_CELL * ncell / (kms[0] * 1e-3) / 1e12
+            out["step_hbm_frac"] = 164.0 * ncell / (ms * 1e-3) / 1e9 / peak_hbm
+        s.close()
+    return dict(workload=W["name"], cells=ncell, unit="cell-updates/s", dtype="f32", value=out["f32"]["value"],
+                ms_per_step=out["f32"]["ms_per_step"], fp64_ms_per_step=out["f64"]["ms_per_step"],
+                fp32_speedup_over_fp64=out["f64"]["ms_per_step"] / out["f32"]["ms_per_step"],
+                step_hbm_frac=out["step_hbm_frac"], explicit_tflops=out["explicit_tflops"], kernels=out["kernels"])
 
 
-def scheme_leg(args, dev, W):
+def kernel_means(s, flush, dev, reps):
+    """Mean ms per launch of each step-kernel class (ch_profile_step: events
+    around every launch, same kernels launched directly), L2 flushed between
+    steps."""
+    import torch
+    from paper_2105_01865_gb300 import capi
+    ksum = [0.0] * 4
+    for _ in range(reps):
+        flush.fill_(1)
+        torch.cuda.synchronize(dev)
+        ms = capi.ch_profile_step(s.handle, 1)
+        ksum = [a + b for a, b in zip(ksum, ms)]
+    return [x / reps for x in ksum]
+
+
+def scheme_leg(args, dev):
     """Time to solution of the paper's split scheme against the standard
     explicit 25-point scheme (Eq. eq-disbi) it replaces (Sec. 4.1 reports
-    dt = 2e-3 against 5e-5 for its shear drop): both FP32, on the bench's
-    shear-drop box, from the same C0 to the same time T = 10 steps of the
-    split scheme, each at its largest stable dt (linear bound x 0.9, CFL
-    0.5 h / max|u|).  Per-kernel times of the standard scheme come from
-    ch_profile_step (chemical potential, advection, update)."""
+    dt = 2e-3 against 5e-5 for its shear drop): both FP32, on the
+    256 x 256 x 128 shear-drop box, from the same C0 to the same time T = 10
+    steps of the split scheme, each at its largest stable dt (linear bound x
+    0.9, CFL 0.5 h / max|u|).  Per-kernel times of the standard scheme come
+    from ch_profile_step (chemical potential, advection, update)."""
     import math
 
     import torch
     from paper_2105_01865_gb300 import capi, inputs, stability
     from paper_2105_01865_gb300.solver import Solver
+    W = SHEAR
     f = inputs.shear_drop_box(W["nx"], W["ny"], W["nz"])
     h, bc, cn, pe = f["h"], f["bc"], f["cn"], f["pe"]
     ncell = W["nx"] * W["ny"] * W["nz"]
@@ -410,13 +474,14 @@ def scheme_leg(args, dev, W):
     return out
 
 
-def dirichlet_leg(args, dev, flush, W):
-    """The bench's shear-drop box with Dirichlet walls (C = 0 on z = 0, 1, the
+def dirichlet_leg(args, dev, flush):
+    """The shear-drop box with Dirichlet walls (C = 0 on z = 0, 1, the
     Rayleigh-Benard setting of Sec. 4.3) instead of no-flux ones: FP32 step
     time, L2 flushed between steps."""
     import torch
     from paper_2105_01865_gb300 import capi, inputs, stability
     from paper_2105_01865_gb300.solver import Solver
+    W = SHEAR
     f = inputs.shear_drop_box(W["nx"], W["ny"], W["nz"])
     h, cn, pe = f["h"], f["cn"], f["pe"]
     bc = (capi.CH_PERIODIC, capi.CH_PERIODIC, capi.CH_DIRICHLET)
@@ -443,12 +508,41 @@ def dirichlet_leg(args, dev, flush, W):
                 bc="x, y periodic; z Dirichlet walls (C = 0)")
 
 
+class HotPath:
+    """One solver of the headline workload and its hot-path step, every stage a
+    call into libch.so: the coarse velocity handed in (ch_set_velocity_coarse),
+    the transfer (ch_interp_to_fine), one RK3 step (ch_step), mass and free
+    energy (ch_mass, ch_free_energy)."""
+
+    def __init__(self, f, prec, dev):
+        import torch
+        from paper_2105_01865_gb300.solver import Solver
+        self.s = Solver(f["shape"], f["h"], f["bc"], f["cn"], f["pe"], f["dt"], f["C"], precision=prec,
+                        coarse_faces=f["faces"], device=dev)
+        self.velc = [self.s._dev(a) for a in f["vel_coarse"]]
+        self.velc_host = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32 if prec == "f32" else np.float64))
+                          .pin_memory() for a in f["vel_coarse"]]
+        self.s._order()
+        self.mass = self.energy = None
+
+    def step(self, _n=1):
+        from paper_2105_01865_gb300 import capi
+        h = self.s.handle
+        capi.ch_set_velocity_coarse(h, *self.velc)
+        capi.ch_interp_to_fine(h)
+        capi.ch_step(h, 1)
+        self.mass = capi.ch_mass(h)
+        self.energy = capi.ch_free_energy(h)
+
+    def launches_per_step(self):
+        return self.s.launches_per_step() + LAUNCHES_AROUND_STEP
+
+
 def gpu_arm(args):
     import torch
     import torch.distributed as dist
 
     from paper_2105_01865_gb300 import build
-    from paper_2105_01865_gb300.solver import Solver
     from paper_2105_01865_gb300 import capi
 
     rank, world, local = _rank()
@@ -462,16 +556,10 @@ def gpu_arm(args):
         dist.barrier()
     capi.load()
 
-    W = WORKLOAD
-    f = workload_inputs(W["nx"], W["ny"], W["nz"])
-    ncell = W["nx"] * W["ny"] * W["nz"]
-
-    def make(prec):
-        s = Solver(f["shape"], f["h"], f["bc"], f["cn"], f["pe"], f["dt"], f["C"], precision=prec, advect=True,
-                   device=dev)
-        s.set_velocity_fine(*f["vel"])
-        return s
-
+    W = HEADLINE
+    f = multires_inputs(W["fine"], W["coarse"], W["ndrops"])
+    nx, ny, nz = W["fine"]
+    ncell = nx * ny * nz
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def barrier():
@@ -480,127 +568,173 @@ def gpu_arm(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    def timed(s, steps, warmup, per_step=None):
+    def timed(hp, steps, warmup, per_step=None):
         """Sum of per-step CUDA-event durations on the solver's stream; L2
         flushed between steps, outside the events."""
-        st = s.stream
+        st = hp.s.stream
         for _ in range(warmup):
-            s.step(1)
+            (per_step or hp.step)(1)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         barrier()
         with torch.cuda.stream(st):
             for a, b in ev:
                 flush.fill_(1)
                 a.record(st)
-                (per_step or s.step)(1)
+                (per_step or hp.step)(1)
                 b.record(st)
         barrier()
         return sum(a.elapsed_time(b) for a, b in ev) / 1e3
 
-    # main FP32 line; nvidia-smi samples the clocks from here through the
-    # batched and multi-resolution legs (all timed regions of this run)
-    s32 = make("f32")
+    def max_ranks(sec):
+        t = torch.tensor([sec], device=dev, dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t)
+
+    # headline: the FP32 hot path on the 1024 x 1024 x 512 workload; nvidia-smi
+    # samples the clocks from here through the last timed leg
+    hp = HotPath(f, "f32", dev)
     clk = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local,
                        args.clocks_dir)
     clk.__enter__()
-    sec = timed(s32, args.steps, args.warmup)
-    s32.sync()
-    sec_t = torch.tensor([sec], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(sec_t, op=dist.ReduceOp.MAX)
-    sec = float(sec_t)
+    sec = max_ranks(timed(hp, args.steps, args.warmup))
+    hp.s.sync()
     value = ncell * args.steps * world / sec
+    ms_step = 1e3 * sec / args.steps
 
-    # per-kernel durations (events around every launch), same L2 flush between steps
-    ksum = [0.0] * 4
-    kreps = max(3, min(args.steps, 10))
-    for _ in range(kreps):
+    # per-launch durations: the step's kernel classes (ch_profile_step), the
+    # transfer's four kernels (ch_profile_interp), the two reductions
+    kms = kernel_means(hp.s, flush, dev, 5)
+    ims = [0.0] * 4
+    for _ in range(3):
         flush.fill_(1)
         torch.cuda.synchronize(dev)
-        ms = capi.ch_profile_step(s32.handle, 1)
-        ksum = [a + b for a, b in zip(ksum, ms)]
-    kms = [x / kreps for x in ksum]
-    names = ["ch_explicit_rhs", "ch_solve_x", "ch_solve_y", "ch_solve_z_update"]
-    # algorithmic bytes per cell of one launch (FP32): the explicit kernel
-    # averages its three substeps (24, 28, 28 B), x/y solves 8 B, z solve +
-    # update 12 B; algorithmic FP32 flops per cell of the explicit kernel
-    # (3 WENO5 face reconstructions of ~75 flops, 7 psi', Laplacian, A_d
-    # fourth differences, divergence and the RK/CN combination)
-    kbytes = [80.0 / 3.0, 8.0, 8.0, 12.0]
-    explicit_flops = 300.0
+        ims = [a + b for a, b in zip(ims, capi.ch_profile_interp(hp.s.handle))]
+    ims = [x / 3 for x in ims]
+    red = []
+    for fn in (capi.ch_mass, capi.ch_free_energy):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(1)
+        torch.cuda.synchronize(dev)
+        a.record(hp.s.stream)
+        fn(hp.s.handle)
+        b.record(hp.s.stream)
+        torch.cuda.synchronize(dev)
+        red.append(a.elapsed_time(b))
+    per_step_sum = 3 * sum(kms) + sum(ims) + sum(red)
     peak_hbm, peak_src = measured_peak_hbm()
-    sm_mhz = 2070.0  # the maximum SM clock; the sampled median is reported in "clocks"
-    peak_fp32 = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12     # TFLOP/s: SMs x FP32 lanes x 2 flops x clock
     traffic = recorded_traffic()
-    achieved = explicit_flops * ncell / (kms[0] * 1e-3) / 1e12
-    roofline = dict(bound="alu", kernel=names[0], achieved=achieved, peak=peak_fp32, unit="TFLOP/s",
-                    frac=achieved / peak_fp32, traffic=traffic.get(names[0]),
-                    peak_source=f"derived: 152 SMs x 128 FP32 lanes x 2 flops x {sm_mhz:.0f} MHz",
-                    kernels={n: dict(ms=m, algo_bytes_per_cell=b, gbs=b * ncell / (m * 1e-3) / 1e9,
-                                     hbm_frac=b * ncell / (m * 1e-3) / 1e9 / peak_hbm,
-                                     hbm_frac_nominal=b * ncell / (m * 1e-3) / 1e9 / NOMINAL_HBM_GBS,
-                                     traffic=traffic.get(n))
-                             for n, m, b in zip(names, kms, kbytes)},
+    achieved = EXPLICIT_FLOPS_PER_CELL * ncell / (kms[0] * 1e-3) / 1e12
+    fine_faces = 3 * ncell * 4  # bytes of fine face velocity written per transfer (FP32)
+    kernels = {n: dict(ms=m, launches_per_step=3, algo_bytes_per_cell=b, gbs=b * ncell / (m * 1e-3) / 1e9,
+                       hbm_frac=b * ncell / (m * 1e-3) / 1e9 / peak_hbm,
+                       hbm_frac_nominal=b * ncell / (m * 1e-3) / 1e9 / NOMINAL_HBM_GBS,
+                       traffic=(traffic[n] * ncell if n in traffic else None))
+               for n, m, b in zip(STEP_KERNELS, kms, STEP_BYTES)}
+    for n, m in zip(INTERP_KERNELS, ims):
+        kernels[n] = dict(ms=m, launches_per_step=1)
+    for n, b in zip(INTERP_KERNELS[1:], (4.0, 4.0, 4.0)):
+        kernels[n].update(algo_bytes_per_cell=b, gbs=b * ncell / (kernels[n]["ms"] * 1e-3) / 1e9,
+                          hbm_frac=b * ncell / (kernels[n]["ms"] * 1e-3) / 1e9 / peak_hbm)
+    kernels["ch_mass"] = dict(ms=red[0], launches_per_step=1, algo_bytes_per_cell=4.0,
+                              hbm_frac=4.0 * ncell / (red[0] * 1e-3) / 1e9 / peak_hbm)
+    kernels["ch_free_energy"] = dict(ms=red[1], launches_per_step=1, algo_bytes_per_cell=4.0,
+                                     hbm_frac=4.0 * ncell / (red[1] * 1e-3) / 1e9 / peak_hbm)
+    share = {n: k["ms"] * k["launches_per_step"] / per_step_sum for n, k in kernels.items()}
+    roofline = dict(bound="alu", kernel=STEP_KERNELS[0], achieved=achieved, peak=PEAK_FP32_TFLOPS, unit="TFLOP/s",
+                    frac=achieved / PEAK_FP32_TFLOPS,
+                    traffic=(traffic[STEP_KERNELS[0]] * ncell if STEP_KERNELS[0] in traffic else None),
+                    flops_per_cell=EXPLICIT_FLOPS_PER_CELL,
+                    peak_source=f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 flops x {SM_MAX_MHZ:.0f} MHz",
+                    kernels=kernels, share_of_kernel_time=share,
+                    kernel_sum_ms=per_step_sum, step_ms=ms_step, kernel_sum_over_step=per_step_sum / ms_step,
+                    step_hbm_frac=(164.0 + 12.0 + 8.0) * ncell / (ms_step * 1e-3) / 1e9 / peak_hbm,
+                    transfer_ms=sum(ims), transfer_fine_faces_gbs=fine_faces / (sum(ims) * 1e-3) / 1e9,
                     hbm_peak=dict(value=peak_hbm, unit="GB/s", source=peak_src, nominal=NOMINAL_HBM_GBS))
 
-    # end to end through the public API with host buffers: pinned H2D of C,
-    # one step, D2H of C, every step
-    hostC = torch.from_numpy(f["C"].astype("float32")).pin_memory()
+    # end to end through the public API with host buffers, every step: pinned
+    # H2D of C and of the coarse velocity, the hot-path step, D2H of C
+    hostC = torch.from_numpy(np.ascontiguousarray(f["C"], dtype=np.float32)).pin_memory()
     outC = torch.empty_like(hostC).pin_memory()
-    s_e2e = make("f32")
+    velc_dev = hp.velc
 
     def e2e_step(_n):
-        s_e2e.C.copy_(hostC, non_blocking=True)
-        s_e2e.step(1)
-        outC.copy_(s_e2e.C, non_blocking=True)
+        st = hp.s.stream
+        with torch.cuda.stream(st):
+            hp.s.C.copy_(hostC, non_blocking=True)
+            for d, hsrc in zip(velc_dev, hp.velc_host):
+                d.copy_(hsrc, non_blocking=True)
+        hp.step(1)
+        with torch.cuda.stream(st):
+            outC.copy_(hp.s.C, non_blocking=True)
 
-    for _ in range(args.warmup):
-        with torch.cuda.stream(s_e2e.stream):
-            e2e_step(1)
-    sec_e2e = timed(s_e2e, args.steps, 0, per_step=e2e_step)
-    t = torch.tensor([sec_e2e], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e = dict(value=ncell * args.steps * world / float(t), unit="cell-updates/s",
-               h2d_bytes_per_step=ncell * 4, d2h_bytes_per_step=ncell * 4)
+    k_e2e = max(3, min(args.steps, 10))
+    sec_e2e = max_ranks(timed(hp, k_e2e, 2, per_step=e2e_step))
+    e2e = dict(value=ncell * k_e2e * world / sec_e2e, unit="cell-updates/s", steps=k_e2e,
+               h2d_bytes_per_step=ncell * 4 + sum(t.numel() * 4 for t in hp.velc_host), d2h_bytes_per_step=ncell * 4)
+    launches = hp.launches_per_step()
+    mass_last = hp.mass
+    hp.s.close()
+    del hp
 
-    batched = batched_leg(args, dev, flush, rank, world)
-    batch_dts = batched.pop("_dts")
-    multires = multires_leg(args, dev, flush) if not args.no_multires else None
-    schemes = scheme_leg(args, dev, W) if not args.no_scheme else None
-    dirichlet = dirichlet_leg(args, dev, flush, W) if not args.no_scheme else None
+    def leg(fn, *a):
+        """A secondary leg; its failure is recorded in the line instead of
+        ending the run (the headline above is already measured)."""
+        try:
+            return fn(*a)
+        except Exception as e:  # noqa: BLE001
+            torch.cuda.synchronize(dev)
+            return dict(error=f"{type(e).__name__}: {e}"[:500])
+
+    def fp64_leg():
+        hp64 = HotPath(f, "f64", dev)
+        k64 = 3
+        sec64 = max_ranks(timed(hp64, k64, 1))
+        hp64.s.close()
+        return dict(ms_per_step=1e3 * sec64 / k64, value=ncell * k64 * world / sec64, unit="cell-updates/s",
+                    steps=k64, fp32_speedup=(1e3 * sec64 / k64) / ms_step)
+
+    extra = not (args.no_extra or args.headline_only)
+    batched, batch_dts = None, None
+    if not args.headline_only:
+        batched = leg(batched_leg, args, dev, flush, rank, world)
+        batch_dts = batched.pop("_dts", None)
+    shear = leg(shear_leg, args, dev, flush) if extra else None
+    schemes = leg(scheme_leg, args, dev) if extra else None
+    dirichlet = leg(dirichlet_leg, args, dev, flush) if extra else None
+    # the plain FP64 GPU hot path on the headline workload: the precision speedup
+    fp64 = leg(fp64_leg) if not args.headline_only else None
     clk.__exit__(None, None, None)
     clocks = clk.summary()
 
-    # the plain FP64 GPU step on the same workload, for the precision speedup
-    s64 = make("f64")
-    k64 = max(3, args.steps // 4)
-    sec64 = timed(s64, k64, min(args.warmup, 3))
-    fp64 = dict(ms_per_step=1e3 * sec64 / k64, value=ncell * k64 / sec64, unit="cell-updates/s",
-                fp32_speedup=(ncell * k64 / sec64) and (value / world) / (ncell * k64 / sec64))
-
     line = dict(metric=METRIC, value=value, unit="cell-updates/s", n_gpus=world, steps=args.steps,
-                warmup=args.warmup, ms_per_step=1e3 * sec / args.steps, higher_is_better=True,
+                warmup=args.warmup, ms_per_step=ms_step, higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
-                config=dict(workload=W["name"], global_batch=world, seq_len=0,
-                            parallelism=f"replicas{world}", cells=ncell, precision="f32 fields, f64 reductions",
-                            l2="flushed between timed steps (256 MB write); working set 235 MB > L2"),
-                roofline=roofline, e2e=e2e, fp64_plain=fp64, batched=batched, multires=multires,
-                scheme_comparison=schemes, dirichlet_walls=dirichlet, clocks=clocks,
-                gpu_launches=args.steps * s32.launches_per_step())
-    if rank == 0 and not args.no_cpu_baseline:
-        if world == 1:
+                config=dict(workload=W["name"], global_batch=world, seq_len=0, parallelism=f"replicas{world}",
+                            cells=ncell, coarse_cells=int(np.prod(W["coarse"])), drops=f["ndrops"],
+                            precision="f32 fields, f64 reductions",
+                            step="coarse velocity in, transfer to the fine mesh, one RK3 step, mass and free energy",
+                            l2="flushed between timed steps (256 MB write); working set ~15 GB > L2"),
+                roofline=roofline, e2e=e2e, fp64_plain=fp64, mass_after=mass_last, batched=batched,
+                shear_drop=shear, scheme_comparison=schemes, dirichlet_walls=dirichlet, clocks=clocks,
+                gpu_launches=args.steps * launches)
+    if rank == 0 and not (args.no_cpu_baseline or args.headline_only):
+        if world == 1 and batch_dts:
             batched["cpu_baseline"] = run_oracle_batch([batch_dts[i] for i in range(len(batch_dts))])
-        cells, times = run_oracle(1, 0)
-        cpu_v = cells * len(times) / sum(times)
-        line["cpu_baseline"] = dict(value=cpu_v, unit="cell-updates/s", cores=1, kind="oracle",
-                                    sample=f"FP64 numpy oracle, one RK3 step of the same shear-drop recipe on a "
-                                           f"{SAMPLE['nx']}x{SAMPLE['ny']}x{SAMPLE['nz']} mesh, single thread, "
-                                           f"host CPU {cpu_model()}")
+        r = run_oracle_multires(1, 1, single=True, pool=(world == 1))
+        single = r["single"]["cells"] * len(r["single"]["times"]) / sum(r["single"]["times"])
+        if "pool" in r:
+            p = r["pool"]
+            line["cpu_baseline"] = dict(value=p["cells"] / p["wall"], unit="cell-updates/s", cores=p["workers"],
+                                        kind="oracle", single_core_value=single,
+                                        sample=sample_text(f", one step in each of {p['workers']} single-threaded "
+                                                           "processes (all cores); single_core_value: one step in "
+                                                           "one process"))
+        else:
+            line["cpu_baseline"] = dict(value=single, unit="cell-updates/s", cores=1, kind="oracle",
+                                        sample=sample_text(", single thread"))
     if rank == 0:
         print(json.dumps(line), flush=True)
-    for s in (s32, s_e2e, s64):
-        s.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -608,14 +742,15 @@ def gpu_arm(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--clocks-dir", default=None, help="directory for the raw nvidia-smi clock samples")
-    ap.add_argument("--no-multires", action="store_true", help="skip the 1024x1024x512 transfer + step leg")
-    ap.add_argument("--no-scheme", action="store_true",
-                    help="skip the split vs standard scheme comparison and the Dirichlet-wall leg")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the shear-drop, scheme-comparison and Dirichlet-wall legs")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="time the headline workload only (no other legs, no FP64 or CPU baseline), for profiling")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

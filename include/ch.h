@@ -96,7 +96,10 @@ typedef struct ch_handle ch_handle;
 /* Bytes of device workspace ch_create needs for these parameters (the
  * explicit terms H of two RK3 substeps, the right-hand side / increment of
  * the factorised solve, the fine face velocity and, with a coarse mesh, the
- * coarse face velocity).  Returns 0 for invalid parameters. */
+ * coarse face velocity).  Returns 0 for invalid parameters.  For inspection
+ * only, the first two regions are, with B = nx ny nz times the element size
+ * rounded up to a multiple of 256: bytes [0, B) hold H of the third substep of
+ * the last split-scheme step, bytes [B, 2B) H of its second substep. */
 size_t ch_workspace_bytes(const ch_params* p);
 
 /* Create a solver for the fine mesh of p (Sec. 3).  C: device array
@@ -134,6 +137,13 @@ int ch_set_velocity_coarse(ch_handle* h, const void* uc, const void* vc, const v
  * (2D Hermite of the coarse face plane there; zero at a wall) -> fine face
  * velocity in the workspace.  Requires a coarse mesh.  Asynchronous. */
 int ch_interp_to_fine(ch_handle* h);
+
+/* Measurement aid: run ch_interp_to_fine once with CUDA events recorded on
+ * the handle's stream around each of its launches, wait, and write their
+ * durations in milliseconds to ms_out[4]: [0] coarse normal gradients,
+ * [1] x integration (u), [2] y integration (v), [3] z integration (w).
+ * Errors: CH_EINVAL (no coarse mesh, NULL), CH_ECUDA. */
+int ch_profile_interp(ch_handle* h, double* ms_out);
 
 /* Copy the workspace's fine face velocity out to device arrays (shapes as
  * for ch_set_velocity_fine).  Asynchronous. */
@@ -243,7 +253,9 @@ int ch_batch_create(const ch_params* boxes, int nbox, void* const* C, void* work
 /* nsteps full RK3 steps of every box.  Persistent schedule: one cooperative
  * launch per step, 12 phases separated by grid barriers whose wait is
  * bounded in time; an expired wait makes the kernel return early and the
- * next ch_batch_sync / ch_batch_mass report CH_ETIMEOUT.  Phased schedule:
+ * next ch_batch_sync / ch_batch_mass report CH_ETIMEOUT.  After a timeout the
+ * boxes' fields are undefined, and later persistent launches return at once
+ * without work until ch_batch_sync has reported and cleared it.  Phased schedule:
  * 12 launches per step.  Both are captured once in a CUDA graph on a user
  * stream.  Asynchronous. */
 int ch_batch_step(ch_batch* b, int64_t nsteps);
@@ -293,9 +305,11 @@ const char* ch_batch_last_error(const ch_batch* b);
  * return CH_EINVAL with a message on stderr.  The array is held by every GPU
  * that loads the library until exit and is shared by all calls: calls that
  * overlap on the GPU race.  Every partial a call reads is written by that
- * call first, so nothing needs clearing.  The first call on a device looks up
- * the array's address with that device current; make it before any stream
- * capture.  Errors: CH_EINVAL, CH_ECUDA. */
+ * call first, so nothing needs clearing.  Every call on a stream that is not
+ * capturing looks up the array's address with the current device (so a device
+ * reset is picked up); a call on a capturing stream reuses the address of the
+ * last such call on that device, so make one call before any stream capture
+ * (else CH_ECUDA).  Errors: CH_EINVAL, CH_ECUDA. */
 int ch_mass_noalloc(const void* C, int64_t nx, int64_t ny, int64_t nz, double h, int precision, double* out,
                     void* stream);
 

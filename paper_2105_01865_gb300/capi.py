@@ -57,6 +57,7 @@ SIGNATURES = [
     ("ch_interp_to_fine", ctypes.c_int, [_P]),
     ("ch_get_velocity_fine", ctypes.c_int, [_P, _P, _P, _P]),
     ("ch_get_interp_tables", ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    ("ch_profile_interp", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     ("ch_restrict_workspace_bytes", ctypes.c_size_t, [_P]),
     ("ch_restrict_to_coarse", ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, _P, _P, _P, _P, _P, _P, _P,
                                              ctypes.c_size_t]),
@@ -174,6 +175,13 @@ def ch_get_velocity_fine(handle, u, v, w):
     _check(load().ch_get_velocity_fine(handle, _ptr(u), _ptr(v), _ptr(w)), handle, "ch_get_velocity_fine")
 
 
+def ch_profile_interp(handle):
+    """ms of [coarse gradients, x, y, z integration] of one ch_interp_to_fine."""
+    out = (ctypes.c_double * 4)()
+    _check(load().ch_profile_interp(handle, out), handle, "ch_profile_interp")
+    return list(out)
+
+
 def ch_get_interp_tables(handle, direction, n):
     start = np.zeros(n, dtype=np.int32)
     wts = np.zeros((n, 4), dtype=np.float64)
@@ -226,8 +234,16 @@ def ch_profile_step(handle, nsteps):
 def ch_mass_noalloc(C, h, out, stream):
     """h^3 sum(C) into the one-element FP64 device tensor ``out`` on ``stream``,
     with no device allocation by the library (scratch is a fixed device array)."""
+    import torch
+    if not (torch.is_tensor(C) and C.is_cuda and C.dim() == 3 and C.is_contiguous()):
+        raise ValueError("ch_mass_noalloc: C must be a contiguous 3D CUDA tensor [nz][ny][nx]")
+    if C.dtype not in (torch.float32, torch.float64):
+        raise ValueError(f"ch_mass_noalloc: C must be float32 or float64, not {C.dtype}")
+    if not (torch.is_tensor(out) and out.is_cuda and out.dtype == torch.float64 and out.numel() >= 1
+            and out.device == C.device):
+        raise ValueError("ch_mass_noalloc: out must be a float64 CUDA tensor of >= 1 element on C's device")
     nz, ny, nx = C.shape
-    prec = CH_F64 if C.element_size() == 8 else CH_F32
+    prec = CH_F64 if C.dtype == torch.float64 else CH_F32
     st = load().ch_mass_noalloc(_ptr(C), nx, ny, nz, h, prec, _ptr(out), ctypes.c_void_p(stream.cuda_stream))
     if st != CH_OK:
         raise CHError(st, f"ch_mass_noalloc: {ch_error_string(st)} (grid limit 268435456 cells)")

@@ -192,6 +192,10 @@ template <int MAXM>
 __global__ void __launch_bounds__(kBThreads, 3) ch_batch_persistent(BatchArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* smem = reinterpret_cast<float*>(smem_raw);
+    // A barrier of an earlier launch gave up and left the arrival counter part
+    // way: run nothing until ch_batch_sync has reported and cleared it (every
+    // CTA reads the same word, written by a launch that has completed).
+    if (*(volatile unsigned*)A.status & kTimeoutFlag) return;
     for (int l = 0; l < kRK; ++l)
         for (int ph = 0; ph < 4; ++ph) {
             run_phase<MAXM>(A, ph, l, smem);

@@ -643,40 +643,45 @@ ch_solve_x(T* __restrict__ a, int64_t nlines, int nx, WCoef<T> cf) {
     solve_x_lines<T, M, L>(a, line0, nlines, nx, cf);
 }
 
-// y- or z-lines (strided).  A CTA of 16 warps owns 32 consecutive x of one
-// outer position: the [n][32] tile is staged through shared memory with
-// coalesced 32-wide rows; element (row j, column c) sits at j*32 + (c ^ (j/M)
-// mod 32), so both the row-wise staging and the per-lane chunk reads of one
-// column are bank-conflict free.  Warp w solves columns w, w + W, ... (W
-// warps per CTA: 16 for short lines, 8 for long ones, which need more
-// registers per lane).  With UPDATE the solved increment is added to C
-// (Eq. eq-fac-3: q^{l+1} = q^l + dq) and non-finite results raise a flag.
+// y- or z-lines (strided).  A CTA of 16 warps owns NC = 32 (or 16)
+// consecutive x of one outer position: the [n][NC] tile is staged through
+// shared memory with coalesced NC-wide rows; element (row j, column c) sits at
+// j*NC + (c ^ (j/M) mod NC), so both the row-wise staging and the per-lane
+// chunk reads of one column are bank-conflict free.  Warp w solves columns
+// w, w + W, ... (W warps per CTA: 16 for short lines, 8 for long ones, which
+// need more registers per lane).  With UPDATE the solved increment is added to
+// C (Eq. eq-fac-3: q^{l+1} = q^l + dq) and non-finite results raise a flag.
+// FP64 lines of 1024 cells use 16-column tiles, so the tile (128 KB) fits the
+// shared memory of a CTA.
 template <typename T, int M>
 struct YZShape {
     static constexpr bool kLong = M * sizeof(T) >= 64;
     static constexpr int kWarps = kLong ? 8 : 16;
     static constexpr int kMinBlocks = kLong ? 1 : 2;
+    static constexpr int kCols = (size_t)32 * M * 32 * sizeof(T) > 227 * 1024 ? 16 : 32;
 };
 
-// One [n][32] tile (tile index = x-block + xblocks * outer) solved by the
-// kYZWarps warps of a CTA; s is the CTA's shared tile of 32 M x 32 values.
-template <typename T, int M, bool UPDATE, int kYZWarps>
+// One [n][NC] tile (tile index = x-block + xblocks * outer) solved by the
+// kYZWarps warps of a CTA; s is the CTA's shared tile of 32 M x NC values.
+template <typename T, int M, bool UPDATE, int kYZWarps, int NC = 32>
 __device__ __forceinline__ void solve_yz_tile(T* a, T* Cf, int nx, int64_t outer_stride,
                                               int64_t line_stride, const WCoef<T>& cf, unsigned int* status,
                                               int64_t tile, T* s) {
+    static_assert(NC == 16 || NC == 32, "tile width");
+    constexpr int kRowsPerPass = kYZWarps * 32 / NC;
     const int n = cf.n;
-    const int xblocks = (nx + 31) >> 5;
+    const int xblocks = (nx + NC - 1) / NC;
     const int xb = (int)(tile % xblocks);
     const int64_t outer = tile / xblocks;
-    const int i0 = xb * 32;
-    const int nl = min(32, nx - i0);
+    const int i0 = xb * NC;
+    const int nl = min(NC, nx - i0);
     const int64_t base = outer * outer_stride + i0;
-    const int tid = threadIdx.x + threadIdx.y * blockDim.x, c = tid & 31, r0 = tid >> 5;
-    auto slot = [&](int j, int col) { return j * 32 + (col ^ ((j / M) & 31)); };
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x, c = tid % NC, r0 = tid / NC;
+    auto slot = [&](int j, int col) { return j * NC + (col ^ ((j / M) & (NC - 1))); };
     __syncthreads();  // the tile may still be read by a previous item of this CTA
     // stage rows asynchronously (zero padding past n and past the ragged x edge)
 #pragma unroll
-    for (int j = r0; j < 32 * M; j += kYZWarps) {
+    for (int j = r0; j < 32 * M; j += kRowsPerPass) {
         if (j < n && c < nl)
             cp_async_elem(&s[slot(j, c)], a + base + (int64_t)j * line_stride + c);
         else
@@ -688,7 +693,7 @@ __device__ __forceinline__ void solve_yz_tile(T* a, T* Cf, int nx, int64_t outer
     const int warp = tid >> 5, lane = tid & 31;
     constexpr int L = LinesPerWarp<T, M>::value;
 #pragma unroll 1
-    for (int col = warp * L; col < 32; col += kYZWarps * L) {
+    for (int col = warp * L; col < NC; col += kYZWarps * L) {
         T v[L][M];
 #pragma unroll
         for (int q = 0; q < L; ++q)
@@ -703,7 +708,7 @@ __device__ __forceinline__ void solve_yz_tile(T* a, T* Cf, int nx, int64_t outer
     __syncthreads();
     bool bad = false;
 #pragma unroll
-    for (int j = r0; j < 32 * M; j += kYZWarps) {
+    for (int j = r0; j < 32 * M; j += kRowsPerPass) {
         if (j < n && c < nl) {
             const int64_t idx = base + (int64_t)j * line_stride + c;
             const T d = s[slot(j, c)];
@@ -726,8 +731,9 @@ ch_solve_yz(T* __restrict__ a, T* __restrict__ Cf, int nx, int64_t outer_stride,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     pdl_wait();
     pdl_launch_dependents();
-    solve_yz_tile<T, M, UPDATE, YZShape<T, M>::kWarps>(a, Cf, nx, outer_stride, line_stride, cf, status, blockIdx.x,
-                                                        reinterpret_cast<T*>(smem_raw));
+    solve_yz_tile<T, M, UPDATE, YZShape<T, M>::kWarps, YZShape<T, M>::kCols>(a, Cf, nx, outer_stride, line_stride, cf,
+                                                                             status, blockIdx.x,
+                                                                             reinterpret_cast<T*>(smem_raw));
 }
 
 // ---------------------------------------------------------------------------
@@ -951,48 +957,102 @@ __device__ __forceinline__ double block_sum(double v) {
     return v;
 }
 
+// Per-lane accumulator of the reductions.  FP64 fields add in FP64.  FP32
+// fields (where FP64 arithmetic, at a small fraction of the FP32 rate on this
+// GPU, would bound the kernel) form every term in FP32 and add it to a
+// double-float pair (s, c): s the rounded FP32 sum, c the exact rounding
+// error of every addition (Knuth's TwoSum, six FP32 operations) summed in
+// FP32.  The pair is flushed to an FP64 total after at most one row segment
+// of 32 terms per lane, so the flushed sums are accurate to about 32^2 u^2
+// (u = 2^-24) of their size and the FP64 total carries the rest.
+template <typename T>
+struct RedAcc {
+    double tot = 0.0;
+    __device__ __forceinline__ void add(double x) { tot += x; }
+    __device__ __forceinline__ void flush() {}
+    __device__ __forceinline__ double total() const { return tot; }
+};
+template <>
+struct RedAcc<float> {
+    double tot = 0.0;
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float t = __fadd_rn(s, x);
+        const float bp = __fsub_rn(t, s);
+        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+        s = t;
+        c = __fadd_rn(c, e);
+    }
+    __device__ __forceinline__ void flush() {
+        tot += (double)s + (double)c;
+        s = c = 0.f;
+    }
+    __device__ __forceinline__ double total() const { return tot + ((double)s + (double)c); }
+};
+
+// Mass h^3 sum C: one warp per x-row (rows split over the grid's warps), lanes
+// stride along the row; each lane flushes its pair after every row.
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
-ch_reduce_mass(const T* __restrict__ C, int64_t N, double* partials, unsigned int* status) {
-    double acc = 0.0;
+ch_reduce_mass(const T* __restrict__ C, int nx, int64_t nrows, double* partials, unsigned int* status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * kRedThreads + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kRedThreads) >> 5;
+    RedAcc<T> acc;
     bool bad = false;
-    for (int64_t e = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; e < N; e += (int64_t)gridDim.x * kRedThreads) {
-        const double c = (double)C[e];
-        bad |= !isfinite(c);
-        acc += c;
+    for (int64_t row = warp0; row < nrows; row += nwarps) {
+        const T* p = C + row * nx;
+        for (int i = lane; i < nx; i += 32) {
+            const T c = p[i];
+            bad |= !isfinite(c);
+            acc.add(c);
+        }
+        acc.flush();
     }
     if (bad) atomicOr(status, 1u);
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+    const double v = block_sum(acc.total());
+    if (threadIdx.x == 0) partials[blockIdx.x] = v;
 }
 
+// Free energy sum [psi(C) + (Cn^2/2) sum_d ((C_{+e_d} - C)/h)^2] (Sec. 1), every
+// term in the field precision: one warp per x-row (k, j), lanes along x; the
+// forward neighbour wraps (periodic), is the cell itself (mirror ghost, zero
+// gradient at a no-flux wall) or its negation (Dirichlet ghost at the top
+// z-wall).
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
-ch_reduce_energy(const T* __restrict__ C, int nx, int ny, int nz, int bcx, int bcy, int bcz, double inv_h,
-                 double half_cn2, double* partials, unsigned int* status) {
-    const int64_t N = (int64_t)nx * ny * nz;
-    double acc = 0.0;
+ch_reduce_energy(const T* __restrict__ C, int nx, int ny, int nz, int bcx, int bcy, int bcz, T inv_h,
+                 T half_cn2, double* partials, unsigned int* status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * kRedThreads + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kRedThreads) >> 5;
+    const int64_t nrows = (int64_t)ny * nz;
+    const int64_t plane = (int64_t)nx * ny;
+    RedAcc<T> acc;
     bool bad = false;
-    for (int64_t e = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; e < N; e += (int64_t)gridDim.x * kRedThreads) {
-        const int i = (int)(e % nx);
-        const int64_t t = e / nx;
-        const int j = (int)(t % ny), k = (int)(t / ny);
-        const double c = (double)C[e];
-        bad |= !isfinite(c);
-        // forward neighbours: wrap, or the mirror ghost (zero gradient) at a wall
-        const int ip = (i + 1 < nx) ? i + 1 : (bcx == CH_PERIODIC ? 0 : i);
+    for (int64_t row = warp0; row < nrows; row += nwarps) {
+        const int j = (int)(row % ny), k = (int)(row / ny);
         const int jp = (j + 1 < ny) ? j + 1 : (bcy == CH_PERIODIC ? 0 : j);
         const int kp = (k + 1 < nz) ? k + 1 : (bcz == CH_PERIODIC ? 0 : k);
-        const double zsign = (k + 1 >= nz && bcz == CH_DIRICHLET) ? -1.0 : 1.0;  // ghost -C at a Dirichlet wall
-        const double gx = ((double)C[e - i + ip] - c) * inv_h;
-        const double gy = ((double)C[e + (int64_t)(jp - j) * nx] - c) * inv_h;
-        const double gz = (zsign * (double)C[e + (int64_t)(kp - k) * nx * ny] - c) * inv_h;
-        const double cc = c * (c - 1.0);
-        acc += 0.25 * cc * cc + half_cn2 * (gx * gx + gy * gy + gz * gz);
+        const T zsign = (k + 1 >= nz && bcz == CH_DIRICHLET) ? T(-1) : T(1);
+        const T* p = C + row * nx;
+        const T* py = C + ((int64_t)k * ny + jp) * nx;
+        const T* pz = C + (int64_t)kp * plane + (int64_t)j * nx;
+        for (int i = lane; i < nx; i += 32) {
+            const int ip = (i + 1 < nx) ? i + 1 : (bcx == CH_PERIODIC ? 0 : i);
+            const T c = p[i];
+            bad |= !isfinite(c);
+            const T gx = (p[ip] - c) * inv_h;
+            const T gy = (py[i] - c) * inv_h;
+            const T gz = (zsign * pz[i] - c) * inv_h;
+            const T cc = c * (c - T(1));
+            acc.add(T(0.25) * cc * cc + half_cn2 * (gx * gx + gy * gy + gz * gz));
+        }
+        acc.flush();
     }
     if (bad) atomicOr(status, 1u);
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+    const double v = block_sum(acc.total());
+    if (threadIdx.x == 0) partials[blockIdx.x] = v;
 }
 
 static __global__ void __launch_bounds__(kRedThreads)

@@ -371,18 +371,22 @@ Tab<T> tab(const ch_handle* h, int d) {
     return t;
 }
 
+// The transfer's four launches; with ev (5 events) an event is recorded
+// before the first and after every launch.
 template <typename T>
-int interp(ch_handle* h) {
+int interp(ch_handle* h, cudaEvent_t* ev = nullptr) {
     const MrArgs a = mr_args(h);
     const double* xf = h->mr_coords;
     const double* yf = xf + h->nc[0] + 1;
     const double* zf = yf + h->nc[1] + 1;
     const int64_t ncell = h->nc[0] * h->nc[1] * h->nc[2];
     const int gblocks = (int)std::min<int64_t>((ncell + kThreads - 1) / kThreads, 8 * 152);
+    if (ev) CHG_CUDA(h, cudaEventRecord(ev[0], h->stream));
     mr_gradients_kernel<T><<<gblocks, kThreads, 0, h->stream>>>(
         (const T*)h->vel_c[0], (const T*)h->vel_c[1], (const T*)h->vel_c[2], xf, yf, zf, a.ncx, a.ncy, a.ncz, a.ncfx,
         a.ncfy, !a.wall[0], !a.wall[1], !a.wall[2], (T*)h->grad_c[0], (T*)h->grad_c[1], (T*)h->grad_c[2]);
     CHG_CUDA(h, cudaGetLastError());
+    if (ev) CHG_CUDA(h, cudaEventRecord(ev[1], h->stream));
     const Tab<T> tx = tab<T>(h, 0), ty = tab<T>(h, 1), tz = tab<T>(h, 2);
     {
         const int64_t warps = (int64_t)a.ny * a.nz;
@@ -397,18 +401,21 @@ int interp(ch_handle* h) {
         mr_integrate_x<T><<<blocks, kMrWarps * 32, smem, h->stream>>>((const T*)h->grad_c[0], (const T*)h->vel_c[0], tx,
                                                                    ty, tz, a, (T*)h->vel[0]);
         CHG_CUDA(h, cudaGetLastError());
+        if (ev) CHG_CUDA(h, cudaEventRecord(ev[2], h->stream));
     }
     {
         const int64_t thr = (int64_t)a.nx * a.nz;
         mr_integrate_yz<T, 1><<<(unsigned)((thr + 255) / 256), 256, 0, h->stream>>>(
             (const T*)h->grad_c[1], (const T*)h->vel_c[1], tx, ty, tz, a, (T*)h->vel[1]);
         CHG_CUDA(h, cudaGetLastError());
+        if (ev) CHG_CUDA(h, cudaEventRecord(ev[3], h->stream));
     }
     {
         const int64_t thr = (int64_t)a.nx * a.ny;
         mr_integrate_yz<T, 2><<<(unsigned)((thr + 255) / 256), 256, 0, h->stream>>>(
             (const T*)h->grad_c[2], (const T*)h->vel_c[2], tx, ty, tz, a, (T*)h->vel[2]);
         CHG_CUDA(h, cudaGetLastError());
+        if (ev) CHG_CUDA(h, cudaEventRecord(ev[4], h->stream));
     }
     return CH_OK;
 }
@@ -487,6 +494,28 @@ int ch_interp_to_fine(ch_handle* h) {
     if (!h) return CH_EINVAL;
     if (!h->nc[0]) return fail(h, CH_EINVAL, "ch_interp_to_fine: no coarse mesh at create");
     return h->prec == CH_F64 ? interp<double>(h) : interp<float>(h);
+}
+
+int ch_profile_interp(ch_handle* h, double* ms_out) {
+    if (!h) return CH_EINVAL;
+    if (!h->nc[0]) return fail(h, CH_EINVAL, "ch_profile_interp: no coarse mesh at create");
+    if (!ms_out) return fail(h, CH_EINVAL, "ch_profile_interp: NULL output");
+    cudaEvent_t ev[5] = {};
+    int rc = CH_OK;
+    for (int i = 0; i < 5 && rc == CH_OK; ++i)
+        if (cudaEventCreate(&ev[i]) != cudaSuccess) rc = fail(h, CH_ECUDA, "ch_profile_interp: cudaEventCreate failed");
+    if (rc == CH_OK) rc = h->prec == CH_F64 ? interp<double>(h, ev) : interp<float>(h, ev);
+    if (rc == CH_OK && cudaEventSynchronize(ev[4]) != cudaSuccess)
+        rc = fail(h, CH_ECUDA, "ch_profile_interp: event wait failed");
+    for (int i = 0; i < 4 && rc == CH_OK; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) != cudaSuccess)
+            rc = fail(h, CH_ECUDA, "ch_profile_interp: cudaEventElapsedTime failed");
+        ms_out[i] = ms;
+    }
+    for (int i = 0; i < 5; ++i)
+        if (ev[i]) cudaEventDestroy(ev[i]);
+    return rc;
 }
 
 int ch_get_interp_tables(ch_handle* h, int dir, int32_t* start, double* weights) {

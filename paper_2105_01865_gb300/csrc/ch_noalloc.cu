@@ -6,9 +6,11 @@
 // to allocate behind its back, or a plug-in that is handed only input and
 // output pointers by its host.  This entry point gives them h^3 * sum(C) with
 // the block partial sums kept in a fixed, file-scope device array instead of
-// allocated scratch.  The first call on each device looks up that array's
-// device address (cudaGetSymbolAddress, with the device current); make that
-// first call before any stream capture.  All calls share the one array, so
+// allocated scratch.  Every call outside a stream capture looks up that
+// array's device address (cudaGetSymbolAddress, with the device current), so a
+// device reset or a new primary context is picked up; a call on a capturing
+// stream reuses the address of the last call on that device, so make one call
+// on the device before any stream capture.  All calls share the one array, so
 // calls whose kernels overlap on the GPU (different streams, or different
 // host threads on one device) race and may return wrong sums.
 #include <cuda_runtime.h>
@@ -66,20 +68,26 @@ __global__ void __launch_bounds__(kThreads) mass_finish(const double* partials, 
     if (threadIdx.x == 0) *out = acc * scale;
 }
 
-// Device address of g_partials on the current device, looked up once per
-// device with that device current.
-cudaError_t partials_for_current_device(double** out) {
+// Device address of g_partials on the current device.  Looked up afresh on
+// every call that is not being captured (the address changes if the device's
+// context is torn down and created again); a capturing call takes the last
+// address looked up on this device and fails if there is none.
+cudaError_t partials_for_current_device(cudaStream_t s, double** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_partials_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_partials);
         if (e != cudaSuccess) return e;
         g_partials_addr[dev] = (double*)p;
     }
+    if (!g_partials_addr[dev]) return cudaErrorStreamCaptureUnsupported;
     *out = g_partials_addr[dev];
     return cudaSuccess;
 }
@@ -100,9 +108,9 @@ extern "C" int ch_mass_noalloc(const void* C, int64_t nx, int64_t ny, int64_t nz
                 (long long)n, (long long)kMaxPartials * kCellsPerBlock, kMaxPartials, (long long)kCellsPerBlock);
         return CH_EINVAL;
     }
-    double* partials = nullptr;
-    if (partials_for_current_device(&partials) != cudaSuccess) return CH_ECUDA;
     cudaStream_t s = (cudaStream_t)stream;
+    double* partials = nullptr;
+    if (partials_for_current_device(s, &partials) != cudaSuccess) return CH_ECUDA;
     if (precision == CH_F64)
         mass_partials<double><<<(unsigned)blocks, kThreads, 0, s>>>((const double*)C, n, partials);
     else

@@ -116,12 +116,9 @@ bool params_valid(const ch_params* p, char* why, size_t wl) {
         }
     }
     // warp-scan line solves: at most 32 x 32 rows per line; the y/z tile
-    // (32 M rows x 32 columns) must fit in shared memory
-    const size_t esz = p->precision == CH_F64 ? 8 : 4;
+    // (32 M rows x 32 columns, 16 for FP64 lines of 1024 cells) fits in
+    // shared memory for every supported length
     if (p->nx > 1024 || p->ny > 1024 || p->nz > 1024) return bad("lines longer than 1024 cells are not supported");
-    for (int64_t n : {p->ny, p->nz})
-        if ((size_t)32 * warp_chunk((int)n) * 32 * esz > kMaxSmem)
-            return bad("y/z line too long for the shared-memory tile in this precision (FP64: <= 512)");
     return true;
 }
 
@@ -191,8 +188,9 @@ int launch_solves_m(ch_handle* h, int l, int dir, T* r, T* Cupd, cudaEvent_t ev_
         constexpr int wpb = 8, lpb = wpb * LinesPerWarp<T, M>::value;
         launch_k(h->stream, ch_solve_x<T, M>, dim3((unsigned)((nlines + lpb - 1) / lpb)), dim3(wpb * 32), 0, r, nlines, nx, cf);
     } else {
-        const unsigned xblocks = (unsigned)((nx + 31) / 32);
-        const size_t shm = (size_t)32 * M * 32 * sizeof(T);
+        constexpr int NC = YZShape<T, M>::kCols;
+        const unsigned xblocks = (unsigned)((nx + NC - 1) / NC);
+        const size_t shm = (size_t)32 * M * NC * sizeof(T);
         if (dir == 1)
             launch_k(h->stream, ch_solve_yz<T, M, false>, dim3(xblocks * (unsigned)nz), dim3(YZShape<T, M>::kWarps * 32), shm,
                 r, nullptr, nx, (int64_t)nx * ny, nx, cf, h->status);
@@ -416,7 +414,7 @@ int launch_solve(ch_handle* h, int l, int dir, T* r, T* Cupd, cudaEvent_t ev_aft
 
 template <typename T, int M>
 int set_attrs_m(ch_handle* h) {
-    const int shm = (int)((size_t)32 * M * 32 * sizeof(T));
+    const int shm = (int)((size_t)32 * M * YZShape<T, M>::kCols * sizeof(T));
     if ((size_t)shm > kMaxSmem) return CH_OK;  // never launched for this precision
     CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_yz<T, M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
     CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_yz<T, M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
@@ -579,10 +577,11 @@ int reduce(ch_handle* h, bool energy, double* out) {
     const ch_params& p = h->p;
     if (energy)
         ch_reduce_energy<T><<<h->red_blocks, kRedThreads, 0, h->stream>>>(
-            (const T*)h->C, (int)h->n[0], (int)h->n[1], (int)h->n[2], p.bc[0], p.bc[1], p.bc[2], 1.0 / p.h,
-            0.5 * p.cn * p.cn, h->red_partials, h->status);
+            (const T*)h->C, (int)h->n[0], (int)h->n[1], (int)h->n[2], p.bc[0], p.bc[1], p.bc[2], (T)(1.0 / p.h),
+            (T)(0.5 * p.cn * p.cn), h->red_partials, h->status);
     else
-        ch_reduce_mass<T><<<h->red_blocks, kRedThreads, 0, h->stream>>>((const T*)h->C, h->ncell, h->red_partials,
+        ch_reduce_mass<T><<<h->red_blocks, kRedThreads, 0, h->stream>>>((const T*)h->C, (int)h->n[0],
+                                                                        h->n[1] * h->n[2], h->red_partials,
                                                                         h->status);
     CHG_CUDA(h, cudaGetLastError());
     ch_reduce_finish<<<1, kRedThreads, 0, h->stream>>>(h->red_partials, h->red_blocks, p.h * p.h * p.h, h->red_out);

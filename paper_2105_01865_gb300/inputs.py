@@ -237,3 +237,27 @@ def batch_boxes(nbox=64, seed=4, sizes=(32, 48, 64, 96, 128), only=None):
         C = drops_field((n, n, n), h, bc, centres, radii, cn) if only is None or only == len(boxes) else None
         boxes.append(dict(shape=(n, n, n), h=h, bc=bc, cn=cn, pe=pe, C=C, vel=None))
     return boxes
+
+
+def multires_box(fine=(1024, 1024, 512), coarse=(256, 256, 128), ndrops=1000, seed=3, stretch=2.0, kmax=8,
+                 rmin=0.01, rmax=0.03):
+    """Multiple-resolution workload (Secs. 3.4, 4.4): a wall-bounded box
+    [0, 2] x [0, 2] x [0, 1] (x, y periodic, no-flux walls at z = 0, 1), a
+    coarse mesh tanh-stretched in z carrying a seeded divergence-free
+    random-Fourier face velocity (max |u| = 1), and a uniform fine mesh of
+    spacing h = 1 / nz_fine holding up to ndrops drops of radius U[rmin, rmax]
+    at seeded positions (pairwise gap and wall gap >= 4 Cn), Cn = 0.75 h,
+    Pe = 0.9 / Cn.  fine and coarse are (nx, ny, nz)."""
+    nx, ny, nz = fine
+    h = 1.0 / nz
+    bc = (PERIODIC, PERIODIC, NOFLUX)
+    cn = 0.75 * h
+    xf = uniform_faces(coarse[0], nx * h)
+    yf = uniform_faces(coarse[1], ny * h)
+    zf = stretched_faces(coarse[2], nz * h, stretch)
+    uc, vc, wc = curl_velocity(xf, yf, zf, bc, seed, kmax=kmax)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    centres, radii = random_drops(rng, ndrops, (nx * h, ny * h, nz * h), rmin, rmax, 4 * cn, (True, True, True))
+    C = drops_field_local((nz, ny, nx), h, centres, radii, cn, 8 * cn)
+    return dict(shape=(nz, ny, nx), h=h, bc=bc, cn=cn, pe=0.9 / cn, faces=(xf, yf, zf), vel_coarse=(uc, vc, wc),
+                C=C, ndrops=len(radii))

@@ -125,6 +125,17 @@ class Solver:
     def launches_per_step(self):
         return capi.ch_launches_per_step(self.handle)
 
+    def explicit_terms(self):
+        """(H^2, H^3): the explicit terms of the second and third RK3 substeps of
+        the last step (split scheme, after at least one step), read from the
+        workspace at the offsets include/ch.h states, as float64 numpy arrays."""
+        self.stream.synchronize()
+        nbytes = self.C.numel() * self.C.element_size()
+        B = (nbytes + 255) // 256 * 256
+        H3 = self.work[:nbytes].view(self.dtype).reshape(self.shape)
+        H2 = self.work[B:B + nbytes].view(self.dtype).reshape(self.shape)
+        return tuple(t.cpu().numpy().astype(np.float64) for t in (H2, H3))
+
     def adjoint(self, C0, nsteps, lam_T, ckpt_every=10):
         """dL/dC0 and dL/dM of nsteps steps from C0, given lam_T = dL/dC_T.
         C0 and lam_T are numpy arrays or CUDA tensors; returns (tensor, float)."""

@@ -7,6 +7,8 @@ import pytest
 from oracle import ch_oracle as co
 from paper_2105_01865_gb300 import inputs
 
+from _parity import assert_parity
+
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
@@ -19,10 +21,6 @@ def _lib():
     from paper_2105_01865_gb300 import build, capi
     build.build()
     capi.load()
-
-
-def rel_l2(a, b):
-    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
 
 
 def flow_2d(nx, ny, h, bc, seed):
@@ -81,7 +79,5 @@ def test_2d_box_matches_oracle(prec, tol, shape, bc, advect):
     p = co.Params(nx, ny, 1, h, cn=cn, pe=pe, dt=dt, bc=bc, w=2.0)
     C0r = C0.astype(np.float32).astype(np.float64) if prec == "f32" else C0
     ref = co.step(C0r, vel, p, 10)
-    err = rel_l2(s.field(), ref)
-    print(f"2D {prec} {shape} {bc} advect={advect}: rel L2 {err:.2e}")
-    assert err <= tol
+    assert_parity(s.field(), ref, tol, f"2D {prec} {shape} {bc} advect={advect}")
     assert abs(s.mass() - m0) <= (1e-13 if prec == "f64" else 1e-6) * abs(m0)

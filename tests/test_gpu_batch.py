@@ -11,6 +11,8 @@ import pytest
 from oracle import ch_oracle as co
 from paper_2105_01865_gb300 import inputs, stability
 
+from _parity import assert_parity
+
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
@@ -95,8 +97,7 @@ def test_batch_matches_oracle_and_conserves_mass():
         nz, ny, nx = box["shape"]
         p = co.Params(nx, ny, nz, box["h"], cn=box["cn"], pe=box["pe"], dt=box["dt"], bc=box["bc"])
         ref = co.step(box["C"], None, p, 5)
-        err = np.linalg.norm(g - ref) / np.linalg.norm(ref)
-        assert err <= 1e-5, (box["shape"], err)
+        assert_parity(g, ref, 1e-5, f"batched box {box['shape']}, 5 steps")
         assert abs(c - a) <= 1e-6 * abs(a)
         assert abs(a - co.mass(box["C"].astype(np.float32).astype(np.float64), p)) <= 1e-12 * abs(a) + 1e-15
 

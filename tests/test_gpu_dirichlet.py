@@ -9,6 +9,8 @@ import pytest
 from oracle import ch_oracle as co
 from paper_2105_01865_gb300 import inputs, stability
 
+from _parity import assert_parity
+
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
@@ -23,10 +25,6 @@ def _lib():
     from paper_2105_01865_gb300 import build, capi
     build.build()
     capi.load()
-
-
-def rel_l2(a, b):
-    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
 
 
 def case(shape, bc, seed, advect):
@@ -67,7 +65,7 @@ def test_fp64_step_matches_oracle(shape, bc, advect):
     nz, ny, nx = shape
     p = co.Params(nx, ny, nz, h, cn=cn, pe=pe, dt=dt, bc=bc)
     ref = co.step(C0, vel, p, 6)
-    assert rel_l2(s.field(), ref) <= 1e-12
+    assert_parity(s.field(), ref, 1e-12, f"FP64 Dirichlet z {shape} {bc}, 6 steps")
     assert abs(s.free_energy() - co.free_energy(ref, p)) <= 1e-12 * abs(co.free_energy(ref, p))
 
 
@@ -79,9 +77,7 @@ def test_fp32_step_matches_oracle():
     nz, ny, nx = shape
     ref = co.step(C0.astype(np.float32).astype(np.float64), vel, co.Params(nx, ny, nz, h, cn=cn, pe=pe, dt=dt,
                                                                           bc=bc), 20)
-    err = rel_l2(s.field(), ref)
-    print(f"FP32 Dirichlet z, 32x20x24, 20 steps: rel L2 {err:.2e}")
-    assert err <= 1e-5
+    assert_parity(s.field(), ref, 1e-5, "FP32 Dirichlet z, 32x20x24, 20 steps")
 
 
 def test_transfer_treats_dirichlet_as_a_wall():

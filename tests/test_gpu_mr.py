@@ -106,3 +106,51 @@ def test_full_size_transfer_sampled_lines_and_divergence():
         line = np.concatenate([[0.0], np.cumsum(G) * h])
         got = w[:, j, i].cpu().numpy().astype(np.float64)
         assert np.abs(got - line).max() <= 2e-6 * scale
+
+
+def test_full_size_multires_step_fp32_against_fp64():
+    """The 1024 x 1024 x 512 multiple-resolution workload in the launch
+    configuration the bench times (velocity transfer from the stretched
+    256 x 256 x 128 mesh, then full RK3 steps with 1024-cell x and y lines and
+    512-cell walled z lines): FP32 against the library's FP64 path, whose
+    kernels the smaller cases pin to the oracle (1024- and 512-cell lines
+    included).  Relative L2 and element bars on C after 1 and 3 steps, the
+    fine velocity, and mass conservation."""
+    from paper_2105_01865_gb300 import stability
+    from paper_2105_01865_gb300.solver import Solver
+    from _parity import K_ELEM
+    f = inputs.multires_box()
+    h, bc, cn, pe = f["h"], f["bc"], f["cn"], f["pe"]
+    dt = min(0.9 * stability.stable_dt(f["shape"], h, bc, cn, pe), 0.5 * h / 1.0)
+    S = {}
+    for prec in ("f32", "f64"):
+        s = Solver(f["shape"], h, bc, cn, pe, dt, f["C"], precision=prec, coarse_faces=f["faces"])
+        s.set_velocity_coarse(*f["vel_coarse"])
+        s.interp_to_fine()
+        S[prec] = s
+    vel = {p: s.velocity_fine() for p, s in S.items()}
+    scale = max(float(t.abs().max()) for t in vel["f64"])
+    for a, b in zip(vel["f32"], vel["f64"]):
+        err = float((a.double() - b).abs().max()) / scale
+        print(f"full-size transfer FP32 vs FP64: max |du| / max|u| = {err:.2e}")
+        assert err <= 2e-6
+    m0 = {p: s.mass() for p, s in S.items()}
+    done = 0
+    for n in (1, 3):
+        for s in S.values():
+            s.step(n - done)
+        done = n
+        for s in S.values():
+            s.sync()
+        a, b = S["f32"].C.double(), S["f64"].C
+        l2 = float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+        em = float((a - b).abs().max() / b.abs().max())
+        print(f"1024x1024x512 multires, {n} steps, FP32 vs FP64: rel L2 {l2:.2e}, max elem {em:.2e}")
+        assert torch.isfinite(a).all()
+        assert l2 <= 1e-6 and em <= K_ELEM * 1e-6
+        del a
+        for p, s in S.items():
+            m = s.mass()
+            assert abs(m - m0[p]) <= (1e-6 if p == "f32" else 1e-12) * abs(m0[p]), (p, n, m, m0[p])
+    for s in S.values():
+        s.close()

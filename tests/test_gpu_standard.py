@@ -10,6 +10,8 @@ import pytest
 from oracle import ch_oracle as co
 from paper_2105_01865_gb300 import inputs, stability
 
+from _parity import assert_parity
+
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
@@ -22,10 +24,6 @@ def _lib():
     from paper_2105_01865_gb300 import build, capi
     build.build()
     capi.load()
-
-
-def rel_l2(a, b):
-    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
 
 
 def make(shape, h, bc, cn, pe, dt, C0, prec, vel=None):
@@ -70,7 +68,7 @@ def test_fp64_matches_oracle(shape, bc, advect):
     s = make(shape, h, bc, cn, pe, dt, C0, "f64", vel)
     s.step(8)
     ref = co.step_standard(C0, vel, params(shape, h, bc, cn, pe, dt), 8)
-    assert rel_l2(s.field(), ref) <= 1e-12
+    assert_parity(s.field(), ref, 1e-12, f"FP64 standard scheme {shape} {bc}, 8 steps")
 
 
 def test_fp32_matches_oracle_and_conserves_mass():
@@ -80,9 +78,7 @@ def test_fp32_matches_oracle_and_conserves_mass():
     m0 = s.mass()
     s.step(40)
     ref = co.step_standard(C0.astype(np.float32).astype(np.float64), vel, params(shape, h, bc, cn, pe, dt), 40)
-    err = rel_l2(s.field(), ref)
-    print(f"FP32 standard scheme 32x20x24, 40 steps: rel L2 on C = {err:.3e}")
-    assert err <= 1e-5
+    assert_parity(s.field(), ref, 1e-5, "FP32 standard scheme 32x20x24, 40 steps")
     assert abs(s.mass() - m0) <= 1e-6 * abs(m0)
 
 
@@ -117,6 +113,4 @@ def test_full_size_shear_drop_one_step():
     s.step(1)
     ref = co.step_standard(f["C"].astype(np.float32).astype(np.float64), f["vel"],
                            params(f["shape"], h, f["bc"], f["cn"], f["pe"], dt), 1)
-    err = rel_l2(s.field(), ref)
-    print(f"FP32 standard scheme 256x256x128, 1 step: rel L2 on C = {err:.3e}")
-    assert err <= 1e-6
+    assert_parity(s.field(), ref, 1e-6, "FP32 standard scheme 256x256x128, 1 step")
