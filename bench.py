@@ -44,9 +44,10 @@ SAMPLE = dict(fine=(128, 128, 64), coarse=(32, 32, 16), ndrops=50)
 SHEAR = dict(name="shear_drop_256x256x128", nx=256, ny=256, nz=128)
 METRIC = "fine-grid CH cell-updates/s"
 L2_FLUSH_BYTES = 256 << 20
-# kernel launches of one hot-path step besides ch_step's own: 4 transfer
-# kernels, 2 for the mass and 2 for the free-energy reduction
-LAUNCHES_AROUND_STEP = 4 + 2 + 2
+# kernel launches of one hot-path step besides ch_step's own: 7 transfer
+# kernels (gradients; plane + line per direction), 2 for the mass and 2 for
+# the free-energy reduction
+LAUNCHES_AROUND_STEP = 7 + 2 + 2
 
 
 def _rank():
@@ -269,7 +270,9 @@ EXPLICIT_FLOPS_PER_CELL = 257.0
 # 80/3; x and y solves 8 B; z solve + update 12 B.
 STEP_KERNELS = ["ch_explicit_rhs", "ch_solve_x", "ch_solve_y", "ch_solve_z_update"]
 STEP_BYTES = [80.0 / 3.0, 8.0, 8.0, 12.0]
-INTERP_KERNELS = ["mr_gradients", "mr_integrate_x", "mr_integrate_y", "mr_integrate_z"]
+# the transfer per direction: interpolation across the lines at the coarse nodes along
+# them, then the integration along the fine lines
+INTERP_KERNELS = ["mr_gradients", "mr_transfer_x", "mr_transfer_y", "mr_transfer_z"]
 
 
 def measured_peak_hbm():

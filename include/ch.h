@@ -84,7 +84,7 @@ typedef struct ch_params {
     /* optional coarse (Navier-Stokes) mesh for the velocity transfer; all 0/NULL if unused.
      * Host arrays of face coordinates, read during ch_create only: xf has ncx+1 entries,
      * starting at 0 and ending at nx*h (likewise y, z).  Any (stretched) spacing;
-     * 4 to 2048 coarse cells per direction. */
+     * 4 to 2048 coarse cells per direction and fewer than 2^31 in all. */
     int64_t ncx, ncy, ncz;
     const double* xf_coarse;
     const double* yf_coarse;

@@ -48,6 +48,7 @@ struct ch_handle {
     void* vel[3];
     void* vel_c[3];     // coarse face velocity
     void* grad_c[3];    // coarse normal gradients
+    void* mr_plane;     // transfer intermediate (y, then z)
     int64_t nc[3];      // coarse cells
     int64_t ncf[3];     // coarse face planes
     // library-owned device memory

@@ -561,6 +561,113 @@ __device__ __forceinline__ void warp_line_solve(T (&v)[M], const WCoef<T>& cf, i
     warp_lines_solve<T, M, 1>(*reinterpret_cast<T(*)[1][M]>(&v), cf, lane);
 }
 
+
+// The same solve of one line with its rows in shared memory: v(i) is a
+// reference to row lane*M + i.  The arithmetic and its order are those of
+// warp_lines_solve with L = 1, so results agree bit for bit; the rows are not
+// held in registers, which keeps lines of 257..1024 cells at a few dozen
+// registers per thread (the register form needs 150 or more), so several
+// CTAs share an SM and hide each other's latency.
+template <typename T, int M, typename V>
+__device__ __forceinline__ void warp_line_solve_sm(V&& v, const WCoef<T>& cf, int lane) {
+    const bool per = cf.periodic;
+    // ---- forward elimination: zero-start pass over the chunk
+    T y1 = T(0), y2 = T(0), acc[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll 8
+    for (int i = 0; i < M; ++i) {
+        const V4<T> c = ld4(cf.fwd + (i * 32 + lane) * 4);
+        const T vi = v(i);
+        const T y = fmadd(-c.x, y1, fmadd(-c.y, y2, vi));
+        y2 = y1;
+        y1 = y;
+        if (per) {
+            const V4<T> w = ld4(cf.W + (i * 32 + lane) * 4);
+            acc[0] = fmadd(w.x, vi, acc[0]);
+            acc[1] = fmadd(w.y, vi, acc[1]);
+            acc[2] = fmadd(w.z, vi, acc[2]);
+            acc[3] = fmadd(w.w, vi, acc[3]);
+        }
+    }
+    // inclusive scan of the chunk end states over lanes 0..lane
+    T q0 = y1, q1 = y2;
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int d = 1 << s;
+        const T o0 = __shfl_up_sync(kFull, q0, d);
+        const T o1 = __shfl_up_sync(kFull, q1, d);
+        if (lane >= d) {
+            const V4<T> P = ld4(cf.Pf + (s * 32 + lane) * 4);
+            q0 = fmadd(P.x, o0, fmadd(P.y, o1, q0));
+            q1 = fmadd(P.z, o0, fmadd(P.w, o1, q1));
+        }
+    }
+    y1 = __shfl_up_sync(kFull, q0, 1);
+    y2 = __shfl_up_sync(kFull, q1, 1);
+    if (lane == 0) y1 = y2 = T(0);
+#pragma unroll 8
+    for (int i = 0; i < M; ++i) {
+        const V4<T> c = ld4(cf.fwd + (i * 32 + lane) * 4);
+        const T y = fmadd(-c.x, y1, fmadd(-c.y, y2, v(i)));
+        y2 = y1;
+        y1 = y;
+        v(i) = fmul(y, c.z);
+    }
+    // ---- Woodbury right-hand side s = S W^T r (warp reduction)
+    T sv[4] = {T(0), T(0), T(0), T(0)};
+    if (per) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[e] += __shfl_xor_sync(kFull, acc[e], o);
+        const V4<T> r0 = ld4(cf.S), r1 = ld4(cf.S + 4), r2 = ld4(cf.S + 8), r3 = ld4(cf.S + 12);
+        sv[0] = dot4(r0, acc);
+        sv[1] = dot4(r1, acc);
+        sv[2] = dot4(r2, acc);
+        sv[3] = dot4(r3, acc);
+    }
+    // ---- back substitution: zero-start pass over the chunk (bottom row first)
+    T x1 = T(0), x2 = T(0);
+#pragma unroll 8
+    for (int i = M - 1; i >= 0; --i) {
+        T u1, u2;
+        ld2(cf.bwd + (i * 32 + lane) * 2, u1, u2);
+        const T x = fmadd(-u1, x1, fmadd(-u2, x2, v(i)));
+        x2 = x1;
+        x1 = x;
+    }
+    // inclusive scan from the last lane down
+    q0 = x1;
+    q1 = x2;
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int d = 1 << s;
+        const T o0 = __shfl_down_sync(kFull, q0, d);
+        const T o1 = __shfl_down_sync(kFull, q1, d);
+        if (lane + d < 32) {
+            const V4<T> P = ld4(cf.Pb + (s * 32 + lane) * 4);
+            q0 = fmadd(P.x, o0, fmadd(P.y, o1, q0));
+            q1 = fmadd(P.z, o0, fmadd(P.w, o1, q1));
+        }
+    }
+    x1 = __shfl_down_sync(kFull, q0, 1);
+    x2 = __shfl_down_sync(kFull, q1, 1);
+    if (lane == 31) x1 = x2 = T(0);
+#pragma unroll 8
+    for (int i = M - 1; i >= 0; --i) {
+        T u1, u2;
+        ld2(cf.bwd + (i * 32 + lane) * 2, u1, u2);
+        const T x = fmadd(-u1, x1, fmadd(-u2, x2, v(i)));
+        x2 = x1;
+        x1 = x;
+        T o = x;
+        if (per) {
+            const V4<T> z = ld4(cf.Z + (i * 32 + lane) * 4);
+            o = fmadd(-z.x, sv[0], fmadd(-z.y, sv[1], fmadd(-z.z, sv[2], fmadd(-z.w, sv[3], o))));
+        }
+        v(i) = o;
+    }
+}
+
 // Lines solved together per warp: CH_SOLVE_LINES (default 2) while a lane
 // holds at most 32 bytes of rows, else one.
 #ifndef CH_SOLVE_LINES
@@ -643,6 +750,78 @@ ch_solve_x(T* __restrict__ a, int64_t nlines, int nx, WCoef<T> cf) {
     solve_x_lines<T, M, L>(a, line0, nlines, nx, cf);
 }
 
+// x-lines of 257..1024 cells (M = 16, 32): one warp per line, the line staged
+// in shared memory with one pad element after every chunk of M rows (lane l's
+// row i at l (M + 1) + i, so the lanes' chunk accesses and the row-wise
+// staging are both free of bank conflicts), and solved there by
+// warp_line_solve_sm.  Rows past nx are zero padding.
+template <typename T, int M>
+struct XSmShape {
+    static constexpr int kStride = M + 1;
+    static constexpr size_t kWarpBytes = (size_t)32 * kStride * sizeof(T);
+    static constexpr int kMinBlocks = (int)((200 * 1024) / (8 * kWarpBytes)) < 1 ? 1
+                                      : ((200 * 1024) / (8 * kWarpBytes) > 4 ? 4 : (200 * 1024) / (8 * kWarpBytes));
+};
+
+template <typename T, int M>
+__global__ void __launch_bounds__(256, XSmShape<T, M>::kMinBlocks)
+ch_solve_x_sm(T* __restrict__ a, int64_t nlines, int nx, WCoef<T> cf) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_wait();
+    pdl_launch_dependents();
+    constexpr int S = XSmShape<T, M>::kStride;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t line = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (line >= nlines) return;  // whole warp
+    T* sv = reinterpret_cast<T*>(smem_raw) + (size_t)warp * 32 * S;
+    T* p = a + line * nx;
+    constexpr int VEC = 16 / sizeof(T);
+    if (nx % VEC == 0) {  // 16-byte vectors (the field is 256-byte aligned, rows are multiples of 16 bytes)
+        for (int e = lane * VEC; e < 32 * M; e += 32 * VEC) {
+            T t[VEC];
+            if (e < nx) {
+                if constexpr (sizeof(T) == 4) {
+                    const float4 g = *reinterpret_cast<const float4*>(p + e);
+                    t[0] = g.x; t[1] = g.y; t[2] = g.z; t[3] = g.w;
+                } else {
+                    const double2 g = *reinterpret_cast<const double2*>(p + e);
+                    t[0] = g.x; t[1] = g.y;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) t[k] = T(0);
+            }
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) sv[((e + k) / M) * S + (e + k) % M] = t[k];
+        }
+    } else {
+        for (int e = lane; e < 32 * M; e += 32) sv[(e / M) * S + e % M] = e < nx ? p[e] : T(0);
+    }
+    __syncwarp();
+    T* mine = sv + lane * S;
+    warp_line_solve_sm<T, M>([&](int i) -> T& { return mine[i]; }, cf, lane);
+    __syncwarp();
+    if (nx % VEC == 0) {
+        for (int e = lane * VEC; e < nx; e += 32 * VEC) {
+            if constexpr (sizeof(T) == 4) {
+                float4 g;
+                g.x = sv[(e / M) * S + e % M];
+                g.y = sv[((e + 1) / M) * S + (e + 1) % M];
+                g.z = sv[((e + 2) / M) * S + (e + 2) % M];
+                g.w = sv[((e + 3) / M) * S + (e + 3) % M];
+                *reinterpret_cast<float4*>(p + e) = g;
+            } else {
+                double2 g;
+                g.x = sv[(e / M) * S + e % M];
+                g.y = sv[((e + 1) / M) * S + (e + 1) % M];
+                *reinterpret_cast<double2*>(p + e) = g;
+            }
+        }
+    } else {
+        for (int e = lane; e < nx; e += 32) p[e] = sv[(e / M) * S + e % M];
+    }
+}
+
 // y- or z-lines (strided).  A CTA of 16 warps owns NC = 32 (or 16)
 // consecutive x of one outer position: the [n][NC] tile is staged through
 // shared memory with coalesced NC-wide rows; element (row j, column c) sits at
@@ -653,12 +832,20 @@ ch_solve_x(T* __restrict__ a, int64_t nlines, int nx, WCoef<T> cf) {
 // C (Eq. eq-fac-3: q^{l+1} = q^l + dq) and non-finite results raise a flag.
 // FP64 lines of 1024 cells use 16-column tiles, so the tile (128 KB) fits the
 // shared memory of a CTA.
+#ifndef CH_YZ_COLS_F32_1024
+#define CH_YZ_COLS_F32_1024 16
+#endif
 template <typename T, int M>
 struct YZShape {
     static constexpr bool kLong = M * sizeof(T) >= 64;
     static constexpr int kWarps = kLong ? 8 : 16;
-    static constexpr int kMinBlocks = kLong ? 1 : 2;
-    static constexpr int kCols = (size_t)32 * M * 32 * sizeof(T) > 227 * 1024 ? 16 : 32;
+    // lines of 257..1024 cells are solved in the tile itself (warp_line_solve_sm)
+    static constexpr bool kSm = M >= 16;
+    static constexpr int kCols = (sizeof(T) == 4 && M == 32) ? CH_YZ_COLS_F32_1024
+                                 : ((size_t)32 * M * 32 * sizeof(T) > 227 * 1024 ? 16 : 32);
+    static constexpr size_t kTileBytes = (size_t)32 * M * kCols * sizeof(T);
+    static constexpr int kSmBlocks = (int)((227 * 1024) / kTileBytes) > 3 ? 3 : (int)((227 * 1024) / kTileBytes);
+    static constexpr int kMinBlocks = kSm ? (kSmBlocks < 1 ? 1 : kSmBlocks) : (kLong ? 1 : 2);
 };
 
 // One [n][NC] tile (tile index = x-block + xblocks * outer) solved by the
@@ -692,6 +879,15 @@ __device__ __forceinline__ void solve_yz_tile(T* a, T* Cf, int nx, int64_t outer
     __syncthreads();
     const int warp = tid >> 5, lane = tid & 31;
     constexpr int L = LinesPerWarp<T, M>::value;
+    if constexpr (M >= 16) {
+        // solved in place in the tile: lane l's row i of column col is at
+        // (l M + i) NC + (col ^ (l mod NC))
+#pragma unroll 1
+        for (int col = warp; col < NC; col += kYZWarps) {
+            T* base = s + (size_t)lane * M * NC + (col ^ (lane & (NC - 1)));
+            warp_line_solve_sm<T, M>([&](int i) -> T& { return base[i * NC]; }, cf, lane);
+        }
+    } else
 #pragma unroll 1
     for (int col = warp * L; col < NC; col += kYZWarps * L) {
         T v[L][M];

@@ -148,10 +148,14 @@ struct MrArgs {
     double h;
 };
 
-template <typename T>
-__device__ __forceinline__ void load_w(const T* __restrict__ w, int i, T* out) {
-#pragma unroll
-    for (int m = 0; m < 4; ++m) out[m] = w[4 * i + m];
+// The 4 weights of entry i of a table (16-byte aligned rows in FP32).
+__device__ __forceinline__ void load_w(const float* __restrict__ w, int i, float* out) {
+    const float4 v = *reinterpret_cast<const float4*>(w + 4 * i);
+    out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+}
+__device__ __forceinline__ void load_w(const double* __restrict__ w, int i, double* out) {
+    const double2 a = *reinterpret_cast<const double2*>(w + 4 * i), b = *reinterpret_cast<const double2*>(w + 4 * i + 2);
+    out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
 }
 
 // Running sum of the integration (step 3).  FP32 keeps a compensation term
@@ -179,19 +183,48 @@ struct RunSum<double> {
     __device__ __forceinline__ double plus(double x) const { return s + x; }
 };
 
-// Step (3) along x: one warp per fine x-line (j, k).  The 64-point stencil
-// is sum-factorised: the warp first contracts the 16 coarse rows of its (y, z)
-// stencil into one coarse x-line g(ix) = sum_{b,c} wy_b wz_c G(ix, sy+b, sz+c)
-// (coalesced over ix, kept in shared memory), then every fine point needs only
-// its 4-point x-stencil of g.  u(face i) = u_ref(j, k) + h sum_{i' < i} Gx(i'),
-// a warp scan per 32-point chunk plus a compensated carry (RunSum).
+__device__ __forceinline__ int wrap_add(int s, int m, int n) {
+    const int k = s + m;
+    return k >= n ? k - n : k;
+}
+
+// Running sum of the integration along a line, carried in blocks: the terms
+// of the current block of up to 32 cells add to a plain partial p, and every
+// full block is folded into a compensated carry (Kahan's summation in FP32,
+// plain in FP64).  A prefix of a 1024-cell line is then within a few
+// roundings of the exact sum without FP64 arithmetic, which is slow on this
+// GPU.
+template <typename T>
+struct BlockSum {
+    RunSum<T> carry;
+    T p = T(0);
+    int n = 0;
+    __device__ __forceinline__ T value() const { return carry.plus(p); }
+    __device__ __forceinline__ void add(T x) {
+        p += x;
+        if (++n == 32) {
+            carry.add(p);
+            p = T(0);
+            n = 0;
+        }
+    }
+};
+
+// Steps (2)-(3) along x: one warp per fine x-line (j, k).  The 64-point
+// stencil is sum-factorised: the warp first contracts the 16 coarse rows of
+// its (y, z) stencil into one coarse x-line g(ix) = sum_{b,c} wy_b wz_c
+// G(ix, sy+b, sz+c) (coalesced over ix, kept in shared memory), then walks the
+// fine line in chunks of 128 cells, 4 consecutive cells per lane: each cell's
+// gradient is the 4-point x-stencil of g; a lane sums its 4 terms, a warp
+// scan of the lane sums gives the chunk's prefix, and a compensated carry
+// joins the chunks (R20).  u(face i) = u_ref(j, k) + h sum_{i' < i} Gx(i').
 constexpr int kMrWarps = 8;
 
 template <typename T>
-__global__ void __launch_bounds__(kMrWarps * 32)
+__global__ void __launch_bounds__(kMrWarps * 32, 4)
 mr_integrate_x(const T* __restrict__ gx, const T* __restrict__ uc, Tab<T> tx, Tab<T> ty, Tab<T> tz, MrArgs a,
                T* __restrict__ u) {
-    extern __shared__ __align__(16) unsigned char mr_smem[];  // kMrWarps coarse lines of ncx values
+    extern __shared__ __align__(16) unsigned char mr_smem[];  // kMrWarps coarse lines of ncx + 3 values
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int warp = blockIdx.x * kMrWarps + wib;
     if (warp >= a.ny * a.nz) return;  // whole warp
@@ -200,20 +233,21 @@ mr_integrate_x(const T* __restrict__ gx, const T* __restrict__ uc, Tab<T> tx, Ta
     load_w(ty.w, j, wy);
     load_w(tz.w, k, wz);
     const int sy = ty.s[j], sz = tz.s[k];
-    T* g = reinterpret_cast<T*>(mr_smem) + (int64_t)wib * a.ncx;
-    for (int ix = lane; ix < a.ncx; ix += 32) {
+    // the coarse line, followed by copies of its first 3 values, so a stencil
+    // starting at sx <= ncx - 1 reads g[sx .. sx + 3] without wrapping
+    T* g = reinterpret_cast<T*>(mr_smem) + (int64_t)wib * (a.ncx + 4);
+    int rows[4][4];  // element offsets of the 16 coarse rows (the coarse mesh has < 2^31 cells)
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) rows[c][b] = (wrap_add(sz, c, a.ncz) * a.ncy + wrap_add(sy, b, a.ncy)) * a.ncx;
+    for (int ix = lane; ix < a.ncx + 3; ix += 32) {
+        const int cx = ix < a.ncx ? ix : ix - a.ncx;
         T acc = T(0);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            int kz = sz + c;
-            kz -= (kz >= a.ncz) ? a.ncz : 0;
-            T accy = T(0);
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                int ky = sy + b;
-                ky -= (ky >= a.ncy) ? a.ncy : 0;
-                accy += wy[b] * gx[((int64_t)kz * a.ncy + ky) * a.ncx + ix];
-            }
+            const T accy = wy[0] * gx[rows[c][0] + cx] + wy[1] * gx[rows[c][1] + cx] + wy[2] * gx[rows[c][2] + cx] +
+                           wy[3] * gx[rows[c][3] + cx];
             acc += wz[c] * accy;
         }
         g[ix] = acc;
@@ -223,125 +257,164 @@ mr_integrate_x(const T* __restrict__ gx, const T* __restrict__ uc, Tab<T> tx, Ta
     __syncwarp();
     T* row = u + ((int64_t)k * a.ny + j) * a.nfx;
     const T hT = (T)a.h;
-    RunSum<T> carry;  // sum over the previous 32-point chunks
-    for (int i0 = 0; i0 < a.nx; i0 += 32) {
-        const int i = i0 + lane;
-        T gv = T(0);
-        if (i < a.nx) {
-            T wx[4];
-            load_w(tx.w, i, wx);
-            const int sx = tx.s[i];
-            T acc = T(0);
+    const bool vec = (a.nx % 4 == 0) && (a.nfx % 4 == 0);
+    RunSum<T> carry;  // sum over the previous chunks
+    for (int i0 = 0; i0 < a.nx; i0 += 128) {
+        const int ib = i0 + 4 * lane;
+        T gv[4];
+        int sxq[4];
+        if (ib + 3 < a.nx) {
+            const int4 s4 = *reinterpret_cast<const int4*>(tx.s + ib);  // 16-byte aligned: ib % 4 == 0
+            sxq[0] = s4.x; sxq[1] = s4.y; sxq[2] = s4.z; sxq[3] = s4.w;
+        } else {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                int kx = sx + q;
-                kx -= (kx >= a.ncx) ? a.ncx : 0;
-                acc += wx[q] * g[kx];
-            }
-            gv = acc;
+            for (int q = 0; q < 4; ++q) sxq[q] = ib + q < a.nx ? tx.s[ib + q] : 0;
         }
-        T incl = gv;  // inclusive scan of the chunk over lanes
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = ib + q;
+            gv[q] = T(0);
+            if (i < a.nx) {
+                T wx[4];
+                load_w(tx.w, i, wx);
+                const T* gs = g + sxq[q];
+                gv[q] = wx[0] * gs[0] + wx[1] * gs[1] + wx[2] * gs[2] + wx[3] * gs[3];
+            }
+        }
+        const T l1 = gv[0], l2 = l1 + gv[1], l3 = l2 + gv[2], tot = l3 + gv[3];
+        T incl = tot;  // inclusive scan of the lane sums
+#pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const T t = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += t;
         }
-        T excl = __shfl_up_sync(0xffffffffu, incl, 1);
-        if (lane == 0) excl = T(0);
-        if (i < a.nx) row[i] = uref + hT * carry.plus(excl);
+        const T base = carry.plus(incl - tot);
+        const T o0 = uref + hT * base, o1 = uref + hT * (base + l1), o2 = uref + hT * (base + l2),
+                o3 = uref + hT * (base + l3);
+        if (vec && ib < a.nx) {
+            if constexpr (sizeof(T) == 4) {
+                *reinterpret_cast<float4*>(row + ib) = make_float4(o0, o1, o2, o3);
+            } else {
+                *reinterpret_cast<double2*>(row + ib) = make_double2(o0, o1);
+                *reinterpret_cast<double2*>(row + ib + 2) = make_double2(o2, o3);
+            }
+        } else {
+            if (ib < a.nx) row[ib] = o0;
+            if (ib + 1 < a.nx) row[ib + 1] = o1;
+            if (ib + 2 < a.nx) row[ib + 2] = o2;
+            if (ib + 3 < a.nx) row[ib + 3] = o3;
+        }
         carry.add(__shfl_sync(0xffffffffu, incl, 31));
     }
     if (a.wall[0] && lane == 0) row[a.nx] = uref + hT * carry.value();
 }
 
-// Contraction of a coarse gradient over the 4 x 4 stencil of the two
-// transverse directions at one coarse index along the marching direction:
-// value(m) = sum_{p,q} wp_p wq_q G(m, sp + p, sq + q) with the index order
-// given by the strides.
-template <typename T>
-__device__ __forceinline__ T contract16(const T* __restrict__ G, int64_t off_m, int sp, int np, int64_t stride_p,
-                                        const T* wp, int sq, int nq, int64_t stride_q, const T* wq) {
-    T acc = T(0);
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-        int kp = sp + p;
-        kp -= (kp >= np) ? np : 0;
-        T accq = T(0);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            int kq = sq + q;
-            kq -= (kq >= nq) ? nq : 0;
-            accq += wq[q] * G[off_m + kp * stride_p + kq * stride_q];
-        }
-        acc += wp[p] * accq;
-    }
-    return acc;
-}
-
-// Steps (2)-(3) along a strided direction (y: v, or z: w): one thread per
-// fine transverse position, marching the fine line.  The transverse 16-point
-// contraction of each coarse index along the line is computed once and kept
-// in a 4-entry window that slides with the fine point's stencil, so a fine
-// point costs 4 FMAs instead of 64 gathers.
+// Step (2) for a strided direction d (y or z), sum-factorised: the coarse
+// gradient of d interpolated by the 4-point Hermite stencils of the two
+// directions across the d-lines (x, and z for d = y or y for d = z) to the
+// fine positions there, at every coarse node along d:
+//   d = y: Py[k][ky][i] = sum_c wz_c(k) sum_q wx_q(i) Gy(sx(i) + q, ky, sz(k) + c),
+//   d = z: Pz[kz][j][i] = sum_b wy_b(j) sum_q wx_q(i) Gz(sx(i) + q, sy(j) + b, kz).
+// One CTA per output row at a time: the non-x contraction of the row's coarse
+// x-line goes to shared memory, then every fine i takes its 4-point x-stencil.
+// The 64-point tri-cubic value at a fine cell is then the 4-point stencil
+// along d of these (mr_line_yz).
 template <typename T, int DIR>
 __global__ void __launch_bounds__(256)
-mr_integrate_yz(const T* __restrict__ G, const T* __restrict__ Vc, Tab<T> tx, Tab<T> ty, Tab<T> tz, MrArgs a,
-                T* __restrict__ out) {
+mr_plane_yz(const T* __restrict__ G, Tab<T> tx, Tab<T> ty, Tab<T> tz, MrArgs a, T* __restrict__ P) {
+    extern __shared__ __align__(16) unsigned char mr_smem[];  // one coarse x-line
+    T* Z = reinterpret_cast<T*>(mr_smem);
+    const int nrows = DIR == 1 ? a.nz * a.ncy : a.ncz * a.ny;
+    for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
+        int64_t rowoff[4];
+        T w[4];
+        if (DIR == 1) {  // r = k ncy + ky: contract z
+            const int k = r / a.ncy, ky = r - k * a.ncy;
+            load_w(tz.w, k, w);
+            const int sz = tz.s[k];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) rowoff[c] = ((int64_t)wrap_add(sz, c, a.ncz) * a.ncy + ky) * a.ncx;
+        } else {         // r = kz ny + j: contract y
+            const int kz = r / a.ny, j = r - kz * a.ny;
+            load_w(ty.w, j, w);
+            const int sy = ty.s[j];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) rowoff[b] = ((int64_t)kz * a.ncy + wrap_add(sy, b, a.ncy)) * a.ncx;
+        }
+        __syncthreads();  // the previous row's Z is no longer read
+        for (int x = threadIdx.x; x < a.ncx; x += blockDim.x)
+            Z[x] = w[0] * G[rowoff[0] + x] + w[1] * G[rowoff[1] + x] + w[2] * G[rowoff[2] + x] +
+                   w[3] * G[rowoff[3] + x];
+        __syncthreads();
+        T* out = P + (int64_t)r * a.nx;
+        for (int i = threadIdx.x; i < a.nx; i += blockDim.x) {
+            T wx[4];
+            load_w(tx.w, i, wx);
+            const int sx = tx.s[i];
+            out[i] = wx[0] * Z[sx] + wx[1] * Z[wrap_add(sx, 1, a.ncx)] + wx[2] * Z[wrap_add(sx, 2, a.ncx)] +
+                     wx[3] * Z[wrap_add(sx, 3, a.ncx)];
+        }
+    }
+}
+
+// Step (3) along a strided direction (y: v, or z: w): one thread per fine
+// transverse position (i, o), marching the fine line.  The 4 values of Py / Pz
+// at the coarse nodes of the current stencil sit in a window that slides with
+// it (one coalesced load per coarse node passed), so a fine cell costs its
+// 4-point stencil along the line, the running sum and one store.
+template <typename T, int DIR>
+__global__ void __launch_bounds__(256)
+mr_line_yz(const T* __restrict__ P, const T* __restrict__ Vc, Tab<T> tx, Tab<T> ty, Tab<T> tz, MrArgs a,
+           T* __restrict__ out) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int nlong = DIR == 1 ? a.ny : a.nz;                 // fine cells along the line
     const int ntr = DIR == 1 ? a.nz : a.ny;                   // second transverse fine size
     if (t >= (int64_t)a.nx * ntr) return;
     const int i = (int)(t % a.nx), o = (int)(t / a.nx);       // fine x and the other transverse index
-    T wxv[4], wov[4];
-    load_w(tx.w, i, wxv);
     const Tab<T>& to = DIR == 1 ? tz : ty;                    // table of the other transverse direction
     const Tab<T>& tl = DIR == 1 ? ty : tz;                    // table along the line
-    load_w(to.w, o, wov);
-    const int sx = tx.s[i], so = to.s[o];
     const int ncl = DIR == 1 ? a.ncy : a.ncz;                 // coarse cells along the line
-    const int nco = DIR == 1 ? a.ncz : a.ncy;                 // coarse cells of the other transverse dir
-    // strides of G[kz][ky][kx]
-    const int64_t st_l = DIR == 1 ? (int64_t)a.ncx : (int64_t)a.ncx * a.ncy;
-    const int64_t st_o = DIR == 1 ? (int64_t)a.ncx * a.ncy : (int64_t)a.ncx;
+    // P address of coarse node m along the line for this thread
+    const T* p0 = DIR == 1 ? P + (int64_t)o * a.ncy * a.nx + i : P + (int64_t)o * a.nx + i;
+    const int64_t pst = DIR == 1 ? (int64_t)a.nx : (int64_t)a.ny * a.nx;
     // reference plane: v at y = 0 (plane [kz][0][kx] of Vc) or w at z = 0
     T ref = T(0);
     if (!a.wall[DIR]) {
+        T wxv[4], wov[4];
+        load_w(tx.w, i, wxv);
+        load_w(to.w, o, wov);
         if (DIR == 1)
-            ref = hermite2(Vc, (int64_t)a.ncfy * a.ncx, (int64_t)1, a.ncz, a.ncx, so, wov, sx, wxv);
+            ref = hermite2(Vc, (int64_t)a.ncfy * a.ncx, (int64_t)1, a.ncz, a.ncx, to.s[o], wov, tx.s[i], wxv);
         else
-            ref = hermite2(Vc, (int64_t)a.ncx, (int64_t)1, a.ncy, a.ncx, so, wov, sx, wxv);
+            ref = hermite2(Vc, (int64_t)a.ncx, (int64_t)1, a.ncy, a.ncx, to.s[o], wov, tx.s[i], wxv);
     }
     T win[4];
     int ws = -1;  // coarse start index of the window
     const T hT = (T)a.h;
-    RunSum<T> run;
-    for (int jl = 0; jl < nlong; ++jl) {
+    BlockSum<T> run;
+    int64_t idx = DIR == 1 ? ((int64_t)o * a.nfy) * a.nx + i : (int64_t)o * a.nx + i;
+    const int64_t ost = DIR == 1 ? (int64_t)a.nx : (int64_t)a.ny * a.nx;  // output stride along the line
+    for (int jl = 0; jl < nlong; ++jl, idx += ost) {
         const int sl = tl.s[jl];
         if (sl != ws) {
-            int first = 0;
-            if (ws >= 0 && sl == (ws + 1 == ncl ? 0 : ws + 1)) {
+            if (ws >= 0 && sl == wrap_add(ws, 1, ncl)) {
                 win[0] = win[1];
                 win[1] = win[2];
                 win[2] = win[3];
-                first = 3;
-            }
-            for (int m = first; m < 4; ++m) {
-                int km = sl + m;
-                km -= (km >= ncl) ? ncl : 0;
-                win[m] = contract16(G, km * st_l, so, nco, st_o, wov, sx, a.ncx, (int64_t)1, wxv);
+                win[3] = p0[wrap_add(sl, 3, ncl) * pst];
+            } else {
+#pragma unroll
+                for (int m = 0; m < 4; ++m) win[m] = p0[wrap_add(sl, m, ncl) * pst];
             }
             ws = sl;
         }
         T wl[4];
         load_w(tl.w, jl, wl);
         const T gval = wl[0] * win[0] + wl[1] * win[1] + wl[2] * win[2] + wl[3] * win[3];
-        const int64_t idx = DIR == 1 ? ((int64_t)o * a.nfy + jl) * a.nx + i : ((int64_t)jl * a.ny + o) * a.nx + i;
         out[idx] = ref + hT * run.value();
         run.add(gval);
     }
-    if (a.wall[DIR]) {
-        const int64_t idx = DIR == 1 ? ((int64_t)o * a.nfy + a.ny) * a.nx + i : ((int64_t)a.nz * a.ny + o) * a.nx + i;
-        out[idx] = ref + hT * run.value();
-    }
+    if (a.wall[DIR]) out[idx] = ref + hT * run.value();
 }
 
 MrArgs mr_args(const ch_handle* h) {
@@ -391,29 +464,35 @@ int interp(ch_handle* h, cudaEvent_t* ev = nullptr) {
     {
         const int64_t warps = (int64_t)a.ny * a.nz;
         const unsigned blocks = (unsigned)((warps + kMrWarps - 1) / kMrWarps);
-        const size_t smem = (size_t)kMrWarps * a.ncx * sizeof(T);
+        const size_t smem = (size_t)kMrWarps * (a.ncx + 4) * sizeof(T);
         static bool attr_set = false;  // one instantiation per T
         if (!attr_set) {
             CHG_CUDA(h, cudaFuncSetAttribute(mr_integrate_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(kMrWarps * kMaxCoarseLine * sizeof(T))));
+                                             (int)(kMrWarps * (kMaxCoarseLine + 4) * sizeof(T))));
             attr_set = true;
         }
-        mr_integrate_x<T><<<blocks, kMrWarps * 32, smem, h->stream>>>((const T*)h->grad_c[0], (const T*)h->vel_c[0], tx,
-                                                                   ty, tz, a, (T*)h->vel[0]);
+        mr_integrate_x<T><<<blocks, kMrWarps * 32, smem, h->stream>>>((const T*)h->grad_c[0], (const T*)h->vel_c[0],
+                                                                      tx, ty, tz, a, (T*)h->vel[0]);
         CHG_CUDA(h, cudaGetLastError());
         if (ev) CHG_CUDA(h, cudaEventRecord(ev[2], h->stream));
     }
+    T* P = (T*)h->mr_plane;
+    const size_t zsm = (size_t)a.ncx * sizeof(T);
     {
+        mr_plane_yz<T, 1><<<16 * 152, 256, zsm, h->stream>>>((const T*)h->grad_c[1], tx, ty, tz, a, P);
+        CHG_CUDA(h, cudaGetLastError());
         const int64_t thr = (int64_t)a.nx * a.nz;
-        mr_integrate_yz<T, 1><<<(unsigned)((thr + 255) / 256), 256, 0, h->stream>>>(
-            (const T*)h->grad_c[1], (const T*)h->vel_c[1], tx, ty, tz, a, (T*)h->vel[1]);
+        mr_line_yz<T, 1><<<(unsigned)((thr + 255) / 256), 256, 0, h->stream>>>(P, (const T*)h->vel_c[1], tx, ty, tz,
+                                                                               a, (T*)h->vel[1]);
         CHG_CUDA(h, cudaGetLastError());
         if (ev) CHG_CUDA(h, cudaEventRecord(ev[3], h->stream));
     }
     {
+        mr_plane_yz<T, 2><<<16 * 152, 256, zsm, h->stream>>>((const T*)h->grad_c[2], tx, ty, tz, a, P);
+        CHG_CUDA(h, cudaGetLastError());
         const int64_t thr = (int64_t)a.nx * a.ny;
-        mr_integrate_yz<T, 2><<<(unsigned)((thr + 255) / 256), 256, 0, h->stream>>>(
-            (const T*)h->grad_c[2], (const T*)h->vel_c[2], tx, ty, tz, a, (T*)h->vel[2]);
+        mr_line_yz<T, 2><<<(unsigned)((thr + 255) / 256), 256, 0, h->stream>>>(P, (const T*)h->vel_c[2], tx, ty, tz,
+                                                                               a, (T*)h->vel[2]);
         CHG_CUDA(h, cudaGetLastError());
         if (ev) CHG_CUDA(h, cudaEventRecord(ev[4], h->stream));
     }

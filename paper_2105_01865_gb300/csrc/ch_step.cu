@@ -39,6 +39,11 @@ constexpr size_t kMaxSmem = 227 * 1024;  // dynamic shared memory per CTA (sm_10
 #ifndef CH_COLUMN_CLUSTER4
 #define CH_COLUMN_CLUSTER4 0
 #endif
+// x-lines of 257..1024 cells solved in shared memory (ch_solve_x_sm) rather
+// than in registers.
+#ifndef CH_X_SM
+#define CH_X_SM 1
+#endif
 // Lines of 65..256 cells also over 2-CTA clusters (CTAs of 4 or 8 warps), so
 // that two tiles share an SM.
 #ifndef CH_COLUMN_CLUSTER_SMALL
@@ -102,6 +107,7 @@ bool params_valid(const ch_params* p, char* why, size_t wl) {
         if (p->nz < 5) return bad("a coarse mesh needs nz >= 5");
         if (p->ncx > kMaxCoarseLine || p->ncy > kMaxCoarseLine || p->ncz > kMaxCoarseLine)
             return bad("coarse mesh has more than 2048 cells in a direction");
+        if ((double)p->ncx * p->ncy * p->ncz >= 2147483647.0) return bad("coarse mesh has 2^31 cells or more");
         if (!p->xf_coarse || !p->yf_coarse || !p->zf_coarse) return bad("coarse face coordinates missing");
         if (!p->advect) return bad("a coarse mesh requires advect = 1");
         const int64_t nf[3] = {p->nx, p->ny, p->nz};
@@ -123,7 +129,7 @@ bool params_valid(const ch_params* p, char* why, size_t wl) {
 }
 
 struct Layout {
-    size_t H0, H1, r, vel[3], velc[3], gradc[3], total;
+    size_t H0, H1, r, vel[3], velc[3], gradc[3], mrplane, total;
 };
 
 Layout layout(const ch_params* p) {
@@ -155,6 +161,9 @@ Layout layout(const ch_params* p) {
         L.velc[1] = take((size_t)nc[2] * ncf[1] * nc[0] * esz);
         L.velc[2] = take((size_t)ncf[2] * nc[1] * nc[0] * esz);
         for (int d = 0; d < 3; ++d) L.gradc[d] = take((size_t)nc[0] * nc[1] * nc[2] * esz);
+        // the transfer's intermediate for y and z (one at a time): the coarse
+        // gradient interpolated across the lines, at the coarse nodes along them
+        L.mrplane = take((size_t)std::max(n[2] * nc[1], nc[2] * n[1]) * (size_t)n[0] * esz);
     }
     L.total = off;
     return L;
@@ -186,7 +195,12 @@ int launch_solves_m(ch_handle* h, int l, int dir, T* r, T* Cupd, cudaEvent_t ev_
     if (dir == 0) {
         const int64_t nlines = (int64_t)ny * nz;
         constexpr int wpb = 8, lpb = wpb * LinesPerWarp<T, M>::value;
-        launch_k(h->stream, ch_solve_x<T, M>, dim3((unsigned)((nlines + lpb - 1) / lpb)), dim3(wpb * 32), 0, r, nlines, nx, cf);
+        if constexpr (M >= 16 && CH_X_SM)
+            launch_k(h->stream, ch_solve_x_sm<T, M>, dim3((unsigned)((nlines + wpb - 1) / wpb)), dim3(wpb * 32),
+                     wpb * XSmShape<T, M>::kWarpBytes, r, nlines, nx, cf);
+        else
+            launch_k(h->stream, ch_solve_x<T, M>, dim3((unsigned)((nlines + lpb - 1) / lpb)), dim3(wpb * 32), 0, r,
+                     nlines, nx, cf);
     } else {
         constexpr int NC = YZShape<T, M>::kCols;
         const unsigned xblocks = (unsigned)((nx + NC - 1) / NC);
@@ -412,8 +426,23 @@ int launch_solve(ch_handle* h, int l, int dir, T* r, T* Cupd, cudaEvent_t ev_aft
     }
 }
 
+#ifndef CH_CARVEOUT_MAX
+#define CH_CARVEOUT_MAX 0
+#endif
 template <typename T, int M>
 int set_attrs_m(ch_handle* h) {
+    if constexpr (M >= 16) {
+        CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_x_sm<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(8 * XSmShape<T, M>::kWarpBytes)));
+        if (CH_CARVEOUT_MAX) {
+            CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_x_sm<T, M>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                             (int)cudaSharedmemCarveoutMaxShared));
+            CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_yz<T, M, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                             (int)cudaSharedmemCarveoutMaxShared));
+            CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_yz<T, M, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                             (int)cudaSharedmemCarveoutMaxShared));
+        }
+    }
     const int shm = (int)((size_t)32 * M * YZShape<T, M>::kCols * sizeof(T));
     if ((size_t)shm > kMaxSmem) return CH_OK;  // never launched for this precision
     CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_yz<T, M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
@@ -635,6 +664,7 @@ int ch_create(const ch_params* p, void* C, void* work, size_t work_bytes, void* 
         for (int d = 0; d < 3; ++d) {
             h->vel_c[d] = wb + L.velc[d];
             h->grad_c[d] = wb + L.gradc[d];
+            h->mr_plane = wb + L.mrplane;
             h->nc[d] = nc[d];
             h->ncf[d] = nc[d] + (p->bc[d] != CH_PERIODIC ? 1 : 0);
         }
