@@ -29,6 +29,8 @@ struct LineTables {
     int periodic;
     const void* col;   // column-solver block (col_layout(nw, R)), or null
     int nw, R;         // column-solver warps per CTA and rows per warp
+    int r0, r1;        // interior rows with constant factors (interior_rows)
+    double k[5];       // their l1, l2, 1/u0, u1/u0, u2/u0
 };
 
 }  // namespace chg

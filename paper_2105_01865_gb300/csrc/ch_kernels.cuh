@@ -354,6 +354,8 @@ struct WCoef {
     const T* __restrict__ S;    // [4][4]      periodic only
     int n;
     int periodic;
+    int r0 = 0, r1 = 0;         // interior rows: constant factors, negligible W, Z (warp_line_solve_sm)
+    T k[5] = {T(0), T(0), T(0), T(0), T(0)};  // their l1, l2, 1/u0, u1/u0, u2/u0
 };
 
 template <typename T>
@@ -564,23 +566,41 @@ __device__ __forceinline__ void warp_line_solve(T (&v)[M], const WCoef<T>& cf, i
 
 // The same solve of one line with its rows in shared memory: v(i) is a
 // reference to row lane*M + i.  The arithmetic and its order are those of
-// warp_lines_solve with L = 1, so results agree bit for bit; the rows are not
-// held in registers, which keeps lines of 257..1024 cells at a few dozen
-// registers per thread (the register form needs 150 or more), so several
-// CTAs share an SM and hide each other's latency.
+// warp_lines_solve with L = 1; the rows are not held in registers, which
+// keeps lines of 257..1024 cells at a few dozen registers per thread (the
+// register form needs 150 or more), so several CTAs share an SM and hide each
+// other's latency.  Interior rows (WCoef r0, r1; see interior_rows) take
+// constant factors from registers, so only the rows near the line's ends load
+// table entries: those loads were the kernel's bottleneck (L1 throughput).
 template <typename T, int M, typename V>
 __device__ __forceinline__ void warp_line_solve_sm(V&& v, const WCoef<T>& cf, int lane) {
     const bool per = cf.periodic;
+    // rows [r0, r1) take the interior constants instead of their table rows
+    // (the tables hold the same values there; W and Z are negligible)
+    auto inner = [&](int i) {
+        const int row = lane * M + i;
+        return row >= cf.r0 && row < cf.r1;
+    };
+    auto fwd = [&](int i) {
+        V4<T> c = {cf.k[0], cf.k[1], cf.k[2], T(0)};
+        if (!inner(i)) c = ld4(cf.fwd + (i * 32 + lane) * 4);
+        return c;
+    };
+    auto bwd = [&](int i, T& u1, T& u2) {
+        u1 = cf.k[3];
+        u2 = cf.k[4];
+        if (!inner(i)) ld2(cf.bwd + (i * 32 + lane) * 2, u1, u2);
+    };
     // ---- forward elimination: zero-start pass over the chunk
     T y1 = T(0), y2 = T(0), acc[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll 8
     for (int i = 0; i < M; ++i) {
-        const V4<T> c = ld4(cf.fwd + (i * 32 + lane) * 4);
+        const V4<T> c = fwd(i);
         const T vi = v(i);
         const T y = fmadd(-c.x, y1, fmadd(-c.y, y2, vi));
         y2 = y1;
         y1 = y;
-        if (per) {
+        if (per && !inner(i)) {
             const V4<T> w = ld4(cf.W + (i * 32 + lane) * 4);
             acc[0] = fmadd(w.x, vi, acc[0]);
             acc[1] = fmadd(w.y, vi, acc[1]);
@@ -606,7 +626,7 @@ __device__ __forceinline__ void warp_line_solve_sm(V&& v, const WCoef<T>& cf, in
     if (lane == 0) y1 = y2 = T(0);
 #pragma unroll 8
     for (int i = 0; i < M; ++i) {
-        const V4<T> c = ld4(cf.fwd + (i * 32 + lane) * 4);
+        const V4<T> c = fwd(i);
         const T y = fmadd(-c.x, y1, fmadd(-c.y, y2, v(i)));
         y2 = y1;
         y1 = y;
@@ -630,7 +650,7 @@ __device__ __forceinline__ void warp_line_solve_sm(V&& v, const WCoef<T>& cf, in
 #pragma unroll 8
     for (int i = M - 1; i >= 0; --i) {
         T u1, u2;
-        ld2(cf.bwd + (i * 32 + lane) * 2, u1, u2);
+        bwd(i, u1, u2);
         const T x = fmadd(-u1, x1, fmadd(-u2, x2, v(i)));
         x2 = x1;
         x1 = x;
@@ -655,12 +675,12 @@ __device__ __forceinline__ void warp_line_solve_sm(V&& v, const WCoef<T>& cf, in
 #pragma unroll 8
     for (int i = M - 1; i >= 0; --i) {
         T u1, u2;
-        ld2(cf.bwd + (i * 32 + lane) * 2, u1, u2);
+        bwd(i, u1, u2);
         const T x = fmadd(-u1, x1, fmadd(-u2, x2, v(i)));
         x2 = x1;
         x1 = x;
         T o = x;
-        if (per) {
+        if (per && !inner(i)) {
             const V4<T> z = ld4(cf.Z + (i * 32 + lane) * 4);
             o = fmadd(-z.x, sv[0], fmadd(-z.y, sv[1], fmadd(-z.z, sv[2], fmadd(-z.w, sv[3], o))));
         }

@@ -161,9 +161,13 @@ Layout layout(const ch_params* p) {
         L.velc[1] = take((size_t)nc[2] * ncf[1] * nc[0] * esz);
         L.velc[2] = take((size_t)ncf[2] * nc[1] * nc[0] * esz);
         for (int d = 0; d < 3; ++d) L.gradc[d] = take((size_t)nc[0] * nc[1] * nc[2] * esz);
-        // the transfer's intermediate for y and z (one at a time): the coarse
+        // the transfer's intermediates, one direction at a time: the coarse
         // gradient interpolated across the lines, at the coarse nodes along them
-        L.mrplane = take((size_t)std::max(n[2] * nc[1], nc[2] * n[1]) * (size_t)n[0] * esz);
+        // (x: nz ncx ny, y: nz ncy nx, z: ncz ny nx), and for x the z-contraction
+        // Qx (nz ncx ncy) after the largest of them
+        const size_t pmax = std::max({(size_t)n[2] * nc[0] * n[1], (size_t)n[2] * nc[1] * n[0],
+                                      (size_t)nc[2] * n[1] * n[0]});
+        L.mrplane = take((pmax + (size_t)n[2] * nc[0] * nc[1]) * esz);
     }
     L.total = off;
     return L;
@@ -183,6 +187,9 @@ WCoef<T> wcoef(const LineTables& lt) {
     k.S = b + L.S;
     k.n = lt.n;
     k.periodic = lt.periodic;
+    k.r0 = lt.r0;
+    k.r1 = lt.r1;
+    for (int m = 0; m < 5; ++m) k.k[m] = (T)lt.k[m];
     return k;
 }
 
@@ -426,23 +433,11 @@ int launch_solve(ch_handle* h, int l, int dir, T* r, T* Cupd, cudaEvent_t ev_aft
     }
 }
 
-#ifndef CH_CARVEOUT_MAX
-#define CH_CARVEOUT_MAX 0
-#endif
 template <typename T, int M>
 int set_attrs_m(ch_handle* h) {
-    if constexpr (M >= 16) {
+    if constexpr (M >= 16)
         CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_x_sm<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(8 * XSmShape<T, M>::kWarpBytes)));
-        if (CH_CARVEOUT_MAX) {
-            CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_x_sm<T, M>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                             (int)cudaSharedmemCarveoutMaxShared));
-            CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_yz<T, M, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                             (int)cudaSharedmemCarveoutMaxShared));
-            CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_yz<T, M, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                             (int)cudaSharedmemCarveoutMaxShared));
-        }
-    }
     const int shm = (int)((size_t)32 * M * YZShape<T, M>::kCols * sizeof(T));
     if ((size_t)shm > kMaxSmem) return CH_OK;  // never launched for this precision
     CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_yz<T, M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
@@ -702,6 +697,10 @@ int ch_create(const ch_params* p, void* C, void* work, size_t work_bytes, void* 
                 lt.n = n;
                 lt.M = mch;
                 lt.periodic = F.periodic;
+                const Interior I = h->esz == 8 ? interior_rows<double>(F) : interior_rows<float>(F);
+                lt.r0 = I.r0;
+                lt.r1 = I.r1;
+                for (int m = 0; m < 5; ++m) lt.k[m] = I.k[m];
                 total += align_up(all.back().size() * h->esz);
                 // y and z lines also get column-solver tables when they fit
                 int nw = 0, R = 0;

@@ -4,6 +4,7 @@
 // solver.  Plain C++, no CUDA: shared by the library and host-only checks.
 #pragma once
 
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <tuple>
@@ -192,6 +193,57 @@ inline LineFactors line_factors(int n, int bc, double ck) {
             F.K[p * 4 + q] = acc;
         }
     return F;
+}
+
+// Interior rows of a factorised line operator: the LU factors of a constant-
+// coefficient banded matrix converge geometrically away from the line's ends,
+// so in the field precision they are exactly constant over a middle range of
+// rows, and the periodic correction vectors W, Z (rows of the inverse banded
+// matrix at the corners) decay there below 2^-80 of their largest entry.
+// Rows [r0, r1) are those where every factor rounds (to the field precision)
+// to its value at row n/2 and W, Z are negligible; k holds those constants
+// (l1, l2, 1/u0, u1/u0, u2/u0).  The solver then uses the constants instead of
+// the per-row tables there and drops the negligible Woodbury terms (whose
+// effect on any output is below 2^-70 of it, far under FP64 rounding).
+struct Interior {
+    int r0 = 0, r1 = 0;
+    double k[5] = {0, 0, 0, 0, 0};
+};
+
+template <typename T>
+Interior interior_rows(const LineFactors& F) {
+    Interior I;
+    const int n = F.n, mid = n / 2;
+    if (n < 8) return I;
+    double wmax = 0.0, zmax = 0.0;
+    if (F.periodic)
+        for (int j = 0; j < 4 * n; ++j) {
+            wmax = std::max(wmax, std::fabs(F.W[j]));
+            zmax = std::max(zmax, std::fabs(F.Z[j]));
+        }
+    const double tiny = std::ldexp(1.0, -80);
+    auto same = [&](int j) {
+        if ((T)F.l1[j] != (T)F.l1[mid] || (T)F.l2[j] != (T)F.l2[mid] || (T)F.dinv[j] != (T)F.dinv[mid] ||
+            (T)F.u1s[j] != (T)F.u1s[mid] || (T)F.u2s[j] != (T)F.u2s[mid])
+            return false;
+        if (F.periodic)
+            for (int m = 0; m < 4; ++m)
+                if (std::fabs(F.W[(size_t)j * 4 + m]) > tiny * wmax || std::fabs(F.Z[(size_t)j * 4 + m]) > tiny * zmax)
+                    return false;
+        return true;
+    };
+    if (!same(mid)) return I;
+    int a = mid, b = mid + 1;
+    while (a > 0 && same(a - 1)) --a;
+    while (b < n && same(b)) ++b;
+    I.r0 = a;
+    I.r1 = b;
+    I.k[0] = F.l1[mid];
+    I.k[1] = F.l2[mid];
+    I.k[2] = F.dinv[mid];
+    I.k[3] = F.u1s[mid];
+    I.k[4] = F.u2s[mid];
+    return I;
 }
 
 // Rows per lane of the warp-scan solver: the smallest power of two M with
