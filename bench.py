@@ -259,12 +259,14 @@ NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal (data sheet); the measured copy
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 PEAK_FP32_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12  # FFMA per lane per clock, 2 flops
 # Algorithmic FP32 flops per cell of one explicit right-hand-side launch with
-# advection (the itemised count of the kernel's arithmetic, minimal form):
-# 3 WENO5 faces x 69 (3 candidates 15, 3 smoothness indicators 33, 3 weights
-# 12, normalised combination 8, flux 1) = 207; divergence 6; psi' 4; 7-point
-# Laplacian 9; M lap psi' + advection 2; the three fourth differences A_d C
-# and their scaled sum 24; RK/CN combination 5 (4 without H^{l-1}).
-EXPLICIT_FLOPS_PER_CELL = 257.0
+# advection (every +, -, x, / of the formulas counted once):
+# 3 WENO5 faces x 68 (candidates 13, second differences 9, first-moment
+# combinations 9, smoothness indicators 18, squares 3, weights 6, normalised
+# combination 9, flux 1) = 204; divergence 6; psi'(C) 4; 7-point Laplacian of
+# psi' 12; H = M lap psi' - div 2; the three fourth differences A_d C and
+# their sum 32; RK/CN combination 5 (3 without H^{l-1} in substep 1).  Mean
+# over the three substeps: 264.
+EXPLICIT_FLOPS_PER_CELL = 264.0
 # Algorithmic bytes per cell of one launch (FP32): explicit = C + u + v + w
 # read, H + r written (24 B), + H^{l-1} read on substeps 2 and 3 (28 B), mean
 # 80/3; x and y solves 8 B; z solve + update 12 B.
@@ -492,6 +494,7 @@ def dirichlet_leg(args, dev, flush):
     s = Solver(f["shape"], h, bc, cn, pe, dt, f["C"], precision="f32", advect=True, device=dev)
     s.set_velocity_fine(*f["vel"])
     st = s.stream
+    m0 = s.mass()
     for _ in range(3):
         s.step(1)
     k = max(3, min(args.steps, 20))
@@ -506,9 +509,12 @@ def dirichlet_leg(args, dev, flush):
     torch.cuda.synchronize(dev)
     ms = sum(a.elapsed_time(b) for a, b in ev) / k
     cells = W["nx"] * W["ny"] * W["nz"]
+    m1 = s.mass()
     s.close()
+    # the walls hold C = 0, so mass leaves through the diffusive wall flux (no
+    # correction is applied: the paper does not specify one)
     return dict(value=cells / (ms * 1e-3), unit="cell-updates/s", ms_per_step=ms, steps=k, dtype="f32",
-                bc="x, y periodic; z Dirichlet walls (C = 0)")
+                bc="x, y periodic; z Dirichlet walls (C = 0)", mass_change=(m1 - m0) / m0, mass_change_steps=k + 3)
 
 
 class HotPath:

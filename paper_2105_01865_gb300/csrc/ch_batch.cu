@@ -101,12 +101,17 @@ __device__ bool grid_barrier(const BatchArgs& A) {
     return ok != 0;
 }
 
-// 16 x-lines: two per warp
+// x-lines solved together by a warp: 2, or more for short lines (a lane then
+// holds 8 rows in all), so the scans of short lines are shared by more rows
+__host__ __device__ constexpr int x_lines_per_warp(int M) { return M >= 4 ? 2 : 8 / M; }
+
+// kBWarps x x_lines_per_warp(M) consecutive x-lines
 template <int M>
 __device__ __forceinline__ void x_item(const BoxDesc& B, int line0, int l) {
+    constexpr int L = x_lines_per_warp(M);
     const int warp = threadIdx.x >> 5;
-    const int64_t line = (int64_t)line0 + 2 * warp;
-    if (line < B.nlines_x) solve_x_lines<float, M, 2>(B.r, line, B.nlines_x, B.nx, B.lines[0][l]);
+    const int64_t line = (int64_t)line0 + L * warp;
+    if (line < B.nlines_x) solve_x_lines<float, M, L>(B.r, line, B.nlines_x, B.nx, B.lines[0][l]);
 }
 
 // one 64-line tile of the two-column solver (y: UPDATE false, z: true)
@@ -326,9 +331,9 @@ int build_items(ch_batch* b) {
                                         std::min(b->zchunk, nz - bz * b->zchunk);
                     lists[0].push_back({cost, make_int4(i, bx, by, bz)});
                 }
-        const int nlx = ny * nz;
-        for (int l0 = 0; l0 < nlx; l0 += 2 * kBWarps)
-            lists[1].push_back({(double)std::min(2 * kBWarps, nlx - l0) * nx, make_int4(i, l0, 0, 0)});
+        const int nlx = ny * nz, xl = x_lines_per_warp(b->boxes[i].M[0]) * kBWarps;
+        for (int l0 = 0; l0 < nlx; l0 += xl)
+            lists[1].push_back({(double)std::min(xl, nlx - l0) * nx, make_int4(i, l0, 0, 0)});
         // y, z: 64-line two-column tiles (w = 1) or 32-column shared-memory tiles (w = 0)
         const BoxDesc& B = b->boxes[i];
         const int xb = (nx + 31) / 32, xb2 = (nx + 63) / 64;

@@ -161,13 +161,9 @@ Layout layout(const ch_params* p) {
         L.velc[1] = take((size_t)nc[2] * ncf[1] * nc[0] * esz);
         L.velc[2] = take((size_t)ncf[2] * nc[1] * nc[0] * esz);
         for (int d = 0; d < 3; ++d) L.gradc[d] = take((size_t)nc[0] * nc[1] * nc[2] * esz);
-        // the transfer's intermediates, one direction at a time: the coarse
+        // the transfer's intermediate for y and z (one at a time): the coarse
         // gradient interpolated across the lines, at the coarse nodes along them
-        // (x: nz ncx ny, y: nz ncy nx, z: ncz ny nx), and for x the z-contraction
-        // Qx (nz ncx ncy) after the largest of them
-        const size_t pmax = std::max({(size_t)n[2] * nc[0] * n[1], (size_t)n[2] * nc[1] * n[0],
-                                      (size_t)nc[2] * n[1] * n[0]});
-        L.mrplane = take((pmax + (size_t)n[2] * nc[0] * nc[1]) * esz);
+        L.mrplane = take((size_t)std::max(n[2] * nc[1], nc[2] * n[1]) * (size_t)n[0] * esz);
     }
     L.total = off;
     return L;
