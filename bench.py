@@ -547,6 +547,65 @@ class HotPath:
         return self.s.launches_per_step() + LAUNCHES_AROUND_STEP
 
 
+def e2e_pipelined(hp, hostC, outC, steps, dev):
+    """`steps` hot-path steps through the public API with host buffers, with
+    the copies pipelined: step n's inputs (C and the coarse velocity) come from
+    pinned host memory into device staging buffers on one copy stream while
+    step n - 1 computes; step n's result C is copied to a device staging
+    buffer and from there to pinned host memory on a second copy stream while
+    step n + 1 computes.  Returns the seconds from the first host-to-device
+    copy to the end of the last device-to-host copy."""
+    import torch
+    st = hp.s.stream
+    h2d, d2h = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    inC = [torch.empty(tuple(hostC.shape), dtype=hp.s.dtype, device=dev) for _ in range(2)]
+    inV = [[torch.empty_like(v) for v in hp.velc] for _ in range(2)]
+    outD = [torch.empty_like(inC[0]) for _ in range(2)]
+    in_ready = [torch.cuda.Event() for _ in range(steps)]
+    in_free, out_free = [None, None], [None, None]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+
+    def upload(n):
+        b = n % 2
+        with torch.cuda.stream(h2d):
+            if in_free[b] is not None:
+                h2d.wait_event(in_free[b])
+            inC[b].copy_(hostC, non_blocking=True)
+            for d, s in zip(inV[b], hp.velc_host):
+                d.copy_(s, non_blocking=True)
+            in_ready[n].record(h2d)
+
+    t0.record(h2d)
+    upload(0)
+    for n in range(steps):
+        b = n % 2
+        st.wait_event(in_ready[n])
+        with torch.cuda.stream(st):
+            hp.s.C.copy_(inC[b], non_blocking=True)
+            for d, s in zip(hp.velc, inV[b]):
+                d.copy_(s, non_blocking=True)
+            in_free[b] = torch.cuda.Event()
+            in_free[b].record(st)
+        if n + 1 < steps:
+            upload(n + 1)
+        hp.step(1)
+        with torch.cuda.stream(st):
+            if out_free[b] is not None:
+                st.wait_event(out_free[b])
+            outD[b].copy_(hp.s.C, non_blocking=True)
+            ready = torch.cuda.Event()
+            ready.record(st)
+        d2h.wait_event(ready)
+        with torch.cuda.stream(d2h):
+            outC.copy_(outD[b], non_blocking=True)
+            out_free[b] = torch.cuda.Event()
+            out_free[b].record(d2h)
+    t1.record(d2h)
+    torch.cuda.synchronize(dev)
+    return t0.elapsed_time(t1) / 1e3
+
+
 def gpu_arm(args):
     import torch
     import torch.distributed as dist
@@ -678,9 +737,16 @@ def gpu_arm(args):
             outC.copy_(hp.s.C, non_blocking=True)
 
     k_e2e = max(3, min(args.steps, 10))
-    sec_e2e = max_ranks(timed(hp, k_e2e, 2, per_step=e2e_step))
+    h2d_bytes = ncell * 4 + sum(t.numel() * 4 for t in hp.velc_host)
+    sec_serial = max_ranks(timed(hp, k_e2e, 2, per_step=e2e_step))
+    sec_e2e = max_ranks(e2e_pipelined(hp, hostC, outC, k_e2e, dev))
     e2e = dict(value=ncell * k_e2e * world / sec_e2e, unit="cell-updates/s", steps=k_e2e,
-               h2d_bytes_per_step=ncell * 4 + sum(t.numel() * 4 for t in hp.velc_host), d2h_bytes_per_step=ncell * 4)
+               h2d_bytes_per_step=h2d_bytes, d2h_bytes_per_step=ncell * 4,
+               pipelined=("every step copies its inputs (C and the coarse velocity) from pinned host memory and "
+                          "its result C back; the copies of step n+1's inputs and of step n's result run on two "
+                          "copy streams during step n"),
+               serial_value=ncell * k_e2e * world / sec_serial,
+               serial="the same copies, not overlapped: H2D, step, D2H in order on one stream")
     launches = hp.launches_per_step()
     mass_last = hp.mass
     hp.s.close()

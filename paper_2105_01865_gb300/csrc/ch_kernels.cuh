@@ -1254,6 +1254,35 @@ ch_reduce_energy(const T* __restrict__ C, int nx, int ny, int nz, int bcx, int b
         const T* p = C + row * nx;
         const T* py = C + ((int64_t)k * ny + jp) * nx;
         const T* pz = C + (int64_t)kp * plane + (int64_t)j * nx;
+        if constexpr (sizeof(T) == 4) {
+            if (nx % 128 == 0) {  // 4 consecutive cells per lane, 16-byte loads (rows are 512-byte multiples)
+                for (int i0 = 4 * lane; i0 < nx; i0 += 128) {
+                    const float4 c4 = *reinterpret_cast<const float4*>(p + i0);
+                    const float4 y4 = *reinterpret_cast<const float4*>(py + i0);
+                    const float4 z4 = *reinterpret_cast<const float4*>(pz + i0);
+                    // the +x neighbour of the lane's last cell: the next lane's first, or past the chunk
+                    float xn = __shfl_down_sync(0xffffffffu, c4.x, 1);
+                    if (lane == 31) {
+                        const int ie = i0 + 4;
+                        xn = ie < nx ? p[ie] : (bcx == CH_PERIODIC ? p[0] : c4.w);
+                    }
+                    const float cv[4] = {c4.x, c4.y, c4.z, c4.w}, xv[4] = {c4.y, c4.z, c4.w, xn};
+                    const float yv[4] = {y4.x, y4.y, y4.z, y4.w}, zv[4] = {z4.x, z4.y, z4.z, z4.w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const T c = cv[q];
+                        bad |= !isfinite(c);
+                        const T gx = (xv[q] - c) * inv_h;
+                        const T gy = (yv[q] - c) * inv_h;
+                        const T gz = (zsign * zv[q] - c) * inv_h;
+                        const T cc = c * (c - T(1));
+                        acc.add(T(0.25) * cc * cc + half_cn2 * (gx * gx + gy * gy + gz * gz));
+                    }
+                }
+                acc.flush();
+                continue;
+            }
+        }
         for (int i = lane; i < nx; i += 32) {
             const int ip = (i + 1 < nx) ? i + 1 : (bcx == CH_PERIODIC ? 0 : i);
             const T c = p[i];
