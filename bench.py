@@ -689,6 +689,22 @@ def gpu_arm(args):
         b.record(hp.s.stream)
         torch.cuda.synchronize(dev)
         red.append(a.elapsed_time(b))
+    # the down-sampling back-coupling (coarse C, rho, mu, F_st; Sec. 3.4) on the
+    # same solver: not part of the step above, timed on its own
+    hp.s.restrict_to_coarse(0.05, 1.0)
+    rms = []
+    for _ in range(3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(1)
+        torch.cuda.synchronize(dev)
+        a.record(hp.s.stream)
+        hp.s.restrict_to_coarse(0.05, 1.0)
+        b.record(hp.s.stream)
+        torch.cuda.synchronize(dev)
+        rms.append(a.elapsed_time(b))
+    restrict = dict(ms=sum(rms) / len(rms), fine_cells=ncell, coarse_cells=int(np.prod(W["coarse"])),
+                    fine_read_gbs=ncell * 4 / (sum(rms) / len(rms) * 1e-3) / 1e9,
+                    outputs="coarse C, rho, mu and the three F_st components")
     per_step_sum = 3 * sum(kms) + sum(ims) + sum(red)
     peak_hbm, peak_src = measured_peak_hbm()
     traffic = recorded_traffic()
@@ -790,7 +806,7 @@ def gpu_arm(args):
                             precision="f32 fields, f64 reductions",
                             step="coarse velocity in, transfer to the fine mesh, one RK3 step, mass and free energy",
                             l2="flushed between timed steps (256 MB write); working set ~15 GB > L2"),
-                roofline=roofline, e2e=e2e, fp64_plain=fp64, mass_after=mass_last, batched=batched,
+                roofline=roofline, e2e=e2e, fp64_plain=fp64, mass_after=mass_last, restrict_to_coarse=restrict, batched=batched,
                 shear_drop=shear, scheme_comparison=schemes, dirichlet_walls=dirichlet, clocks=clocks,
                 gpu_launches=args.steps * launches)
     if rank == 0 and not (args.no_cpu_baseline or args.headline_only):
