@@ -863,7 +863,8 @@ struct YZShape {
     static constexpr bool kSm = M >= 16;
     static constexpr int kCols = (sizeof(T) == 4 && M == 32) ? CH_YZ_COLS_F32_1024
                                  : ((size_t)32 * M * 32 * sizeof(T) > 227 * 1024 ? 16 : 32);
-    static constexpr size_t kTileBytes = (size_t)32 * M * kCols * sizeof(T);
+    // tiles solved in place carry one pad element after every lane chunk of M rows
+    static constexpr size_t kTileBytes = ((size_t)32 * M * kCols + (kSm ? 32 : 0)) * sizeof(T);
     static constexpr int kSmBlocks = (int)((227 * 1024) / kTileBytes) > 3 ? 3 : (int)((227 * 1024) / kTileBytes);
     static constexpr int kMinBlocks = kSm ? (kSmBlocks < 1 ? 1 : kSmBlocks) : (kLong ? 1 : 2);
 };
@@ -884,7 +885,17 @@ __device__ __forceinline__ void solve_yz_tile(T* a, T* Cf, int nx, int64_t outer
     const int nl = min(NC, nx - i0);
     const int64_t base = outer * outer_stride + i0;
     const int tid = threadIdx.x + threadIdx.y * blockDim.x, c = tid % NC, r0 = tid / NC;
-    auto slot = [&](int j, int col) { return j * NC + (col ^ ((j / M) & (NC - 1))); };
+    // Layout: long lines (M >= 16, solved in place) put lane chunk l (rows
+    // l M .. l M + M - 1) at l (M NC + 1), rows of NC contiguous: lane l's row i
+    // of any column is then in bank (l + i NC + col) mod 32, distinct over the
+    // warp, and the row-wise staging is contiguous.  Short lines (copied to
+    // registers) swizzle the column by the chunk index instead.
+    auto slot = [&](int j, int col) {
+        if constexpr (M >= 16)
+            return j * NC + j / M + col;
+        else
+            return j * NC + (col ^ ((j / M) & (NC - 1)));
+    };
     __syncthreads();  // the tile may still be read by a previous item of this CTA
     // stage rows asynchronously (zero padding past n and past the ragged x edge)
 #pragma unroll
@@ -904,7 +915,7 @@ __device__ __forceinline__ void solve_yz_tile(T* a, T* Cf, int nx, int64_t outer
         // (l M + i) NC + (col ^ (l mod NC))
 #pragma unroll 1
         for (int col = warp; col < NC; col += kYZWarps) {
-            T* base = s + (size_t)lane * M * NC + (col ^ (lane & (NC - 1)));
+            T* base = s + (size_t)lane * (M * NC + 1) + col;
             warp_line_solve_sm<T, M>([&](int i) -> T& { return base[i * NC]; }, cf, lane);
         }
     } else

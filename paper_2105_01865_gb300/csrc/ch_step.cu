@@ -207,7 +207,7 @@ int launch_solves_m(ch_handle* h, int l, int dir, T* r, T* Cupd, cudaEvent_t ev_
     } else {
         constexpr int NC = YZShape<T, M>::kCols;
         const unsigned xblocks = (unsigned)((nx + NC - 1) / NC);
-        const size_t shm = (size_t)32 * M * NC * sizeof(T);
+        const size_t shm = YZShape<T, M>::kTileBytes;
         if (dir == 1)
             launch_k(h->stream, ch_solve_yz<T, M, false>, dim3(xblocks * (unsigned)nz), dim3(YZShape<T, M>::kWarps * 32), shm,
                 r, nullptr, nx, (int64_t)nx * ny, nx, cf, h->status);
@@ -434,7 +434,7 @@ int set_attrs_m(ch_handle* h) {
     if constexpr (M >= 16)
         CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_x_sm<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(8 * XSmShape<T, M>::kWarpBytes)));
-    const int shm = (int)((size_t)32 * M * YZShape<T, M>::kCols * sizeof(T));
+    const int shm = (int)YZShape<T, M>::kTileBytes;
     if ((size_t)shm > kMaxSmem) return CH_OK;  // never launched for this precision
     CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_yz<T, M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
     CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_yz<T, M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
