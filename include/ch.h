@@ -190,6 +190,12 @@ int ch_mass(ch_handle* h, double* out);
  * accumulated in FP64.  Waits for the stream; *out is a host double. */
 int ch_free_energy(ch_handle* h, double* out);
 
+/* Both diagnostics of Sec. 4.3 / Sec. 1 in one pass over C: *mass as ch_mass and
+ * *free_energy as ch_free_energy (host doubles; the same FP64 results up to the
+ * order of the additions).  Waits for the stream.  Errors: CH_EINVAL (NULL),
+ * CH_ENONFINITE (a NaN/Inf in C), CH_ECUDA. */
+int ch_diagnostics(ch_handle* h, double* mass, double* free_energy);
+
 /* Wait for the handle's stream and report (then clear) the non-finite flag. */
 int ch_sync(ch_handle* h);
 

@@ -64,6 +64,7 @@ SIGNATURES = [
     ("ch_step", ctypes.c_int, [_P, ctypes.c_int64]),
     ("ch_mass", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     ("ch_free_energy", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    ("ch_diagnostics", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     ("ch_sync", ctypes.c_int, [_P]),
     ("ch_launches_per_step", ctypes.c_int, [_P]),
     ("ch_profile_step", ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]),
@@ -214,6 +215,13 @@ def ch_free_energy(handle):
     out = ctypes.c_double()
     _check(load().ch_free_energy(handle, ctypes.byref(out)), handle, "ch_free_energy")
     return out.value
+
+
+def ch_diagnostics(handle):
+    """(mass, free energy) from one pass over C."""
+    m, e = ctypes.c_double(), ctypes.c_double()
+    _check(load().ch_diagnostics(handle, ctypes.byref(m), ctypes.byref(e)), handle, "ch_diagnostics")
+    return m.value, e.value
 
 
 def ch_sync(handle):

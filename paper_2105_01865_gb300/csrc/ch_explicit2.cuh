@@ -167,6 +167,9 @@ __device__ __forceinline__ Pr<T> face_flux_p(Pr<T> vel, Pr<T> m3, Pr<T> m2, Pr<T
 #ifndef CH_EXPLICIT_TZ
 #define CH_EXPLICIT_TZ 10
 #endif
+#ifndef CH_EXPLICIT_TZ_DEEP
+#define CH_EXPLICIT_TZ_DEEP 16
+#endif
 #ifndef CH_EXPLICIT_STAGE_OFFSETS
 #define CH_EXPLICIT_STAGE_OFFSETS 1
 #endif
@@ -175,7 +178,20 @@ __device__ __forceinline__ Pr<T> face_flux_p(Pr<T> vel, Pr<T> m3, Pr<T> m2, Pr<T
 #endif
 constexpr int kTX2 = 64;               // cells in x per CTA (two per thread)
 constexpr int kTZ2 = CH_EXPLICIT_TZ;   // z-planes marched per CTA
+constexpr int kTZ2Deep = CH_EXPLICIT_TZ_DEEP;
 constexpr int kHL2 = 4;   // left halo columns (even, so thread pairs stay 8/16-byte aligned)
+
+// z-planes marched per CTA for an nx x ny x nz field.  A tile reads 4 halo
+// planes besides its own, so a deep tile re-reads less of C; a shallow one
+// gives more CTAs.  The FP32 path takes the deep tile when that still leaves
+// at least 8 full waves of 3 CTAs on each of the 152 SMs (on large meshes,
+// where the re-read dominates); the results do not depend on the depth (every
+// face flux is formed by the same arithmetic in whichever tile forms it).
+inline int explicit_zchunk(int nx, int ny, int nz, bool fp32) {
+    const int64_t xy = (int64_t)((nx + kTX2 - 1) / kTX2) * ((ny + kTY - 1) / kTY);
+    const int64_t deep = xy * ((nz + kTZ2Deep - 1) / kTZ2Deep);
+    return (fp32 && deep >= 8 * 3 * 152) ? kTZ2Deep : kTZ2;
+}
 
 // One 64 x 8 x zchunk tile (tile coordinates bx, by, bz) computed by the 256
 // threads of a CTA; called by the standalone kernel below and by the batched
@@ -446,14 +462,16 @@ __device__ __forceinline__ void explicit_tile2(const T* C, const T* u, const T* 
     }
 }
 
-template <typename T, bool ADV, bool DIRI>
+// TZ: z-planes per CTA, a compile-time constant (a runtime depth cost 2 % on
+// the 256 x 256 x 128 shear drop).
+template <typename T, bool ADV, bool DIRI, int TZ>
 __global__ void __launch_bounds__(32 * kTY, sizeof(T) == 4 ? CH_EXPLICIT_MIN_BLOCKS : 2)
 ch_explicit_rhs2(const T* __restrict__ C, const T* __restrict__ u, const T* __restrict__ v,
                  const T* __restrict__ w, const T* __restrict__ Hprev, T* __restrict__ Hout, T* __restrict__ r,
                  RhsArgs<T> a) {
     pdl_wait();
     pdl_launch_dependents();
-    explicit_tile2<T, ADV, DIRI>(C, u, v, w, Hprev, Hout, r, a, blockIdx.x, blockIdx.y, blockIdx.z, kTZ2);
+    explicit_tile2<T, ADV, DIRI>(C, u, v, w, Hprev, Hout, r, a, blockIdx.x, blockIdx.y, blockIdx.z, TZ);
 }
 
 }  // namespace chg

@@ -128,6 +128,11 @@ __device__ __forceinline__ void cp_async_pair(float* smem, const float* gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
+// 16 bytes (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async_16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
@@ -775,12 +780,15 @@ ch_solve_x(T* __restrict__ a, int64_t nlines, int nx, WCoef<T> cf) {
 // row i at l (M + 1) + i, so the lanes' chunk accesses and the row-wise
 // staging are both free of bank conflicts), and solved there by
 // warp_line_solve_sm.  Rows past nx are zero padding.
+#ifndef CH_XSM_MAX_BLOCKS
+#define CH_XSM_MAX_BLOCKS 4
+#endif
 template <typename T, int M>
 struct XSmShape {
     static constexpr int kStride = M + 1;
     static constexpr size_t kWarpBytes = (size_t)32 * kStride * sizeof(T);
-    static constexpr int kMinBlocks = (int)((200 * 1024) / (8 * kWarpBytes)) < 1 ? 1
-                                      : ((200 * 1024) / (8 * kWarpBytes) > 4 ? 4 : (200 * 1024) / (8 * kWarpBytes));
+    static constexpr int kFit = (int)((200 * 1024) / (8 * kWarpBytes));  // CTAs whose buffers fit an SM
+    static constexpr int kMinBlocks = kFit < 1 ? 1 : (kFit > CH_XSM_MAX_BLOCKS ? CH_XSM_MAX_BLOCKS : kFit);
 };
 
 template <typename T, int M>
@@ -855,17 +863,26 @@ ch_solve_x_sm(T* __restrict__ a, int64_t nlines, int nx, WCoef<T> cf) {
 #ifndef CH_YZ_COLS_F32_1024
 #define CH_YZ_COLS_F32_1024 16
 #endif
+#ifndef CH_YZ_COLS_F32_512
+#define CH_YZ_COLS_F32_512 32
+#endif
+#ifndef CH_YZ_MAX_BLOCKS
+#define CH_YZ_MAX_BLOCKS 3
+#endif
 template <typename T, int M>
 struct YZShape {
     static constexpr bool kLong = M * sizeof(T) >= 64;
     static constexpr int kWarps = kLong ? 8 : 16;
     // lines of 257..1024 cells are solved in the tile itself (warp_line_solve_sm)
     static constexpr bool kSm = M >= 16;
-    static constexpr int kCols = (sizeof(T) == 4 && M == 32) ? CH_YZ_COLS_F32_1024
+    static constexpr int kCols = (sizeof(T) == 4 && M == 32)   ? CH_YZ_COLS_F32_1024
+                                 : (sizeof(T) == 4 && M == 16) ? CH_YZ_COLS_F32_512
                                  : ((size_t)32 * M * 32 * sizeof(T) > 227 * 1024 ? 16 : 32);
     // tiles solved in place carry one pad element after every lane chunk of M rows
     static constexpr size_t kTileBytes = ((size_t)32 * M * kCols + (kSm ? 32 : 0)) * sizeof(T);
-    static constexpr int kSmBlocks = (int)((227 * 1024) / kTileBytes) > 3 ? 3 : (int)((227 * 1024) / kTileBytes);
+    static constexpr int kSmBlocks = (int)((227 * 1024) / kTileBytes) > CH_YZ_MAX_BLOCKS
+                                         ? CH_YZ_MAX_BLOCKS
+                                         : (int)((227 * 1024) / kTileBytes);
     static constexpr int kMinBlocks = kSm ? (kSmBlocks < 1 ? 1 : kSmBlocks) : (kLong ? 1 : 2);
 };
 
@@ -961,6 +978,389 @@ ch_solve_yz(T* __restrict__ a, T* __restrict__ Cf, int nx, int64_t outer_stride,
     solve_yz_tile<T, M, UPDATE, YZShape<T, M>::kWarps, YZShape<T, M>::kCols>(a, Cf, nx, outer_stride, line_stride, cf,
                                                                              status, blockIdx.x,
                                                                              reinterpret_cast<T*>(smem_raw));
+}
+
+// L adjacent values of one row as one shared- or global-memory vector access
+// (L = 1, 2 or 4 floats, 1 or 2 doubles; the address is L-element aligned).
+template <typename T, int L>
+__device__ __forceinline__ void vld(const T* p, T (&v)[L]) {
+    if constexpr (L == 1) {
+        v[0] = *p;
+    } else if constexpr (L == 2 && sizeof(T) == 4) {
+        const float2 t = *reinterpret_cast<const float2*>(p);
+        v[0] = t.x; v[1] = t.y;
+    } else if constexpr (L == 2) {
+        const double2 t = *reinterpret_cast<const double2*>(p);
+        v[0] = t.x; v[1] = t.y;
+    } else {
+        static_assert(L == 4 && sizeof(T) == 4, "vector width");
+        const float4 t = *reinterpret_cast<const float4*>(p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+}
+template <typename T, int L>
+__device__ __forceinline__ void vst(T* p, const T (&v)[L]) {
+    if constexpr (L == 1) {
+        *p = v[0];
+    } else if constexpr (L == 2 && sizeof(T) == 4) {
+        *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+    } else if constexpr (L == 2) {
+        *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    } else {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+}
+// cp.async of L adjacent elements (4 L or 8 L bytes, both addresses aligned to that size)
+template <typename T, int L>
+__device__ __forceinline__ void cp_async_vec(T* smem, const T* gmem) {
+    constexpr int kBytes = L * (int)sizeof(T);
+    if constexpr (kBytes == 16) {
+        cp_async_16(smem, gmem);
+    } else {
+        const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(kBytes) : "memory");
+    }
+}
+
+// warp_line_solve_sm for L lines of the same operator at once: row i of the
+// lane's chunk holds the L lines' values side by side at p + i * stride, so
+// one L-wide shared-memory access serves every line and the L recurrences are
+// independent chains; the interior test, the table loads of the end rows and
+// the scans' span matrices are shared by the L lines.  Each line's arithmetic
+// is that of warp_line_solve_sm, in the same order, so the results agree with
+// it bit for bit.
+template <typename T, int M, int L>
+__device__ __forceinline__ void warp_lines_solve_smv(T* p, int stride, const WCoef<T>& cf, int lane) {
+    const bool per = cf.periodic;
+    const int lo = cf.r0 - lane * M, hi = cf.r1 - lane * M;  // this chunk's interior rows: [lo, hi)
+    auto inner = [&](int i) { return i >= lo && i < hi; };
+    auto fwd = [&](int i) {
+        V4<T> c = {cf.k[0], cf.k[1], cf.k[2], T(0)};
+        if (!inner(i)) c = ld4(cf.fwd + (i * 32 + lane) * 4);
+        return c;
+    };
+    auto bwd = [&](int i, T& u1, T& u2) {
+        u1 = cf.k[3];
+        u2 = cf.k[4];
+        if (!inner(i)) ld2(cf.bwd + (i * 32 + lane) * 2, u1, u2);
+    };
+    // ---- forward elimination: zero-start pass over the chunk
+    T y1[L], y2[L], acc[L][4];
+#pragma unroll
+    for (int q = 0; q < L; ++q) {
+        y1[q] = y2[q] = T(0);
+        acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = T(0);
+    }
+#pragma unroll 8
+    for (int i = 0; i < M; ++i) {
+        const V4<T> c = fwd(i);
+        T vi[L];
+        vld<T, L>(p + i * stride, vi);
+#pragma unroll
+        for (int q = 0; q < L; ++q) {
+            const T y = fmadd(-c.x, y1[q], fmadd(-c.y, y2[q], vi[q]));
+            y2[q] = y1[q];
+            y1[q] = y;
+        }
+        if (per && !inner(i)) {
+            const V4<T> w = ld4(cf.W + (i * 32 + lane) * 4);
+#pragma unroll
+            for (int q = 0; q < L; ++q) {
+                acc[q][0] = fmadd(w.x, vi[q], acc[q][0]);
+                acc[q][1] = fmadd(w.y, vi[q], acc[q][1]);
+                acc[q][2] = fmadd(w.z, vi[q], acc[q][2]);
+                acc[q][3] = fmadd(w.w, vi[q], acc[q][3]);
+            }
+        }
+    }
+    // inclusive scan of the chunk end states over lanes 0..lane
+    T q0[L], q1[L];
+#pragma unroll
+    for (int q = 0; q < L; ++q) {
+        q0[q] = y1[q];
+        q1[q] = y2[q];
+    }
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int d = 1 << s;
+        T o0[L], o1[L];
+#pragma unroll
+        for (int q = 0; q < L; ++q) {
+            o0[q] = __shfl_up_sync(kFull, q0[q], d);
+            o1[q] = __shfl_up_sync(kFull, q1[q], d);
+        }
+        if (lane >= d) {
+            const V4<T> P = ld4(cf.Pf + (s * 32 + lane) * 4);
+#pragma unroll
+            for (int q = 0; q < L; ++q) {
+                q0[q] = fmadd(P.x, o0[q], fmadd(P.y, o1[q], q0[q]));
+                q1[q] = fmadd(P.z, o0[q], fmadd(P.w, o1[q], q1[q]));
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < L; ++q) {
+        y1[q] = __shfl_up_sync(kFull, q0[q], 1);
+        y2[q] = __shfl_up_sync(kFull, q1[q], 1);
+        if (lane == 0) y1[q] = y2[q] = T(0);
+    }
+#pragma unroll 8
+    for (int i = 0; i < M; ++i) {
+        const V4<T> c = fwd(i);
+        T vi[L];
+        vld<T, L>(p + i * stride, vi);
+#pragma unroll
+        for (int q = 0; q < L; ++q) {
+            const T y = fmadd(-c.x, y1[q], fmadd(-c.y, y2[q], vi[q]));
+            y2[q] = y1[q];
+            y1[q] = y;
+            vi[q] = fmul(y, c.z);
+        }
+        vst<T, L>(p + i * stride, vi);
+    }
+    // ---- Woodbury right-hand side s = S W^T r (warp reduction)
+    T sv[L][4];
+#pragma unroll
+    for (int q = 0; q < L; ++q) sv[q][0] = sv[q][1] = sv[q][2] = sv[q][3] = T(0);
+    if (per) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < L; ++q)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[q][e] += __shfl_xor_sync(kFull, acc[q][e], o);
+        const V4<T> r0 = ld4(cf.S), r1 = ld4(cf.S + 4), r2 = ld4(cf.S + 8), r3 = ld4(cf.S + 12);
+#pragma unroll
+        for (int q = 0; q < L; ++q) {
+            sv[q][0] = dot4(r0, acc[q]);
+            sv[q][1] = dot4(r1, acc[q]);
+            sv[q][2] = dot4(r2, acc[q]);
+            sv[q][3] = dot4(r3, acc[q]);
+        }
+    }
+    // ---- back substitution: zero-start pass over the chunk (bottom row first)
+    T x1[L], x2[L];
+#pragma unroll
+    for (int q = 0; q < L; ++q) x1[q] = x2[q] = T(0);
+#pragma unroll 8
+    for (int i = M - 1; i >= 0; --i) {
+        T u1, u2;
+        bwd(i, u1, u2);
+        T vi[L];
+        vld<T, L>(p + i * stride, vi);
+#pragma unroll
+        for (int q = 0; q < L; ++q) {
+            const T x = fmadd(-u1, x1[q], fmadd(-u2, x2[q], vi[q]));
+            x2[q] = x1[q];
+            x1[q] = x;
+        }
+    }
+    // inclusive scan from the last lane down
+#pragma unroll
+    for (int q = 0; q < L; ++q) {
+        q0[q] = x1[q];
+        q1[q] = x2[q];
+    }
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int d = 1 << s;
+        T o0[L], o1[L];
+#pragma unroll
+        for (int q = 0; q < L; ++q) {
+            o0[q] = __shfl_down_sync(kFull, q0[q], d);
+            o1[q] = __shfl_down_sync(kFull, q1[q], d);
+        }
+        if (lane + d < 32) {
+            const V4<T> P = ld4(cf.Pb + (s * 32 + lane) * 4);
+#pragma unroll
+            for (int q = 0; q < L; ++q) {
+                q0[q] = fmadd(P.x, o0[q], fmadd(P.y, o1[q], q0[q]));
+                q1[q] = fmadd(P.z, o0[q], fmadd(P.w, o1[q], q1[q]));
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < L; ++q) {
+        x1[q] = __shfl_down_sync(kFull, q0[q], 1);
+        x2[q] = __shfl_down_sync(kFull, q1[q], 1);
+        if (lane == 31) x1[q] = x2[q] = T(0);
+    }
+#pragma unroll 8
+    for (int i = M - 1; i >= 0; --i) {
+        T u1, u2;
+        bwd(i, u1, u2);
+        T vi[L];
+        vld<T, L>(p + i * stride, vi);
+        const bool edge = per && !inner(i);
+        V4<T> z = {T(0), T(0), T(0), T(0)};
+        if (edge) z = ld4(cf.Z + (i * 32 + lane) * 4);
+#pragma unroll
+        for (int q = 0; q < L; ++q) {
+            const T x = fmadd(-u1, x1[q], fmadd(-u2, x2[q], vi[q]));
+            x2[q] = x1[q];
+            x1[q] = x;
+            T o = x;
+            if (edge) o = fmadd(-z.x, sv[q][0], fmadd(-z.y, sv[q][1], fmadd(-z.z, sv[q][2], fmadd(-z.w, sv[q][3], o))));
+            vi[q] = o;
+        }
+        vst<T, L>(p + i * stride, vi);
+    }
+}
+
+// y- or z-lines of 257..1024 cells, L adjacent lines per warp.  A CTA of
+// NC / L warps owns NC consecutive x of one outer position; the [n][NC] tile
+// sits in shared memory with lane chunk l (rows l M .. l M + M - 1) at
+// l (M NC + L), rows of NC contiguous, and every L-column group of a row
+// L-element aligned.  Staging and write-back move L adjacent columns per
+// access (cp.async of 4 L bytes, vector stores), and warp w solves columns
+// w L .. w L + L - 1 in the tile (warp_lines_solve_smv).  Lane l's L-wide
+// access to row i lands in words (l L + 16 i + w L) mod 32 + 0..L-1: within
+// each group of 32 / L lanes that the hardware serves together those are
+// distinct, so the solve passes are free of bank conflicts.  Needs nx a
+// multiple of L.  With UPDATE the increment is added to C and non-finite
+// results raise the status flag.
+// At most MAXB CTAs per SM (fewer where the tiles do not fit).
+template <typename T, int M, int L, int NC, int MAXB>
+struct YZVShape {
+    static constexpr int kWarps = NC / L;
+    static constexpr size_t kTileBytes = ((size_t)32 * M * NC + (size_t)32 * L) * sizeof(T);
+    static constexpr int kFit = (int)((227 * 1024) / kTileBytes);
+    static constexpr int kMinBlocks = kFit < 1 ? 1 : (kFit > MAXB ? MAXB : kFit);
+};
+
+template <typename T, int M, bool UPDATE, int L, int NC, int MAXB>
+__global__ void __launch_bounds__(NC / L * 32, (YZVShape<T, M, L, NC, MAXB>::kMinBlocks))
+ch_solve_yz_v(T* __restrict__ a, T* __restrict__ Cf, int nx, int64_t outer_stride, int64_t line_stride,
+              WCoef<T> cf, unsigned int* status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_wait();
+    pdl_launch_dependents();
+    static_assert(NC % L == 0 && M * NC % 32 == 0, "tile shape");
+    constexpr int G = NC / L;           // column groups of a row = warps of the CTA
+    constexpr int kChunk = M * NC + L;  // elements of one lane chunk with its pad
+    T* s = reinterpret_cast<T*>(smem_raw);
+    const int n = cf.n;
+    const int xblocks = (nx + NC - 1) / NC;
+    const int xb = (int)(blockIdx.x % xblocks);
+    const int64_t outer = blockIdx.x / xblocks;
+    const int i0 = xb * NC;
+    const int nl = min(NC, nx - i0);  // a multiple of L
+    const int64_t base = outer * outer_stride + i0;
+    const int tid = threadIdx.x, g = tid % G, rr = tid / G;  // column group g, rows rr, rr + 32, ...
+    const int c = g * L;
+    auto slot = [&](int j) { return (j / M) * kChunk + (j % M) * NC + c; };
+#pragma unroll 4
+    for (int j = rr; j < 32 * M; j += 32) {
+        if (j < n && c < nl) {
+            cp_async_vec<T, L>(s + slot(j), a + base + (int64_t)j * line_stride + c);
+        } else {
+            T z[L];
+#pragma unroll
+            for (int q = 0; q < L; ++q) z[q] = T(0);
+            vst<T, L>(s + slot(j), z);
+        }
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    const int warp = tid >> 5, lane = tid & 31;
+    warp_lines_solve_smv<T, M, L>(s + (size_t)lane * kChunk + warp * L, NC, cf, lane);
+    __syncthreads();
+    bool bad = false;
+#pragma unroll 4
+    for (int j = rr; j < n; j += 32) {
+        if (c < nl) {
+            const int64_t idx = base + (int64_t)j * line_stride + c;
+            T d[L];
+            vld<T, L>(s + slot(j), d);
+            if (UPDATE) {
+                T cv[L];
+                vld<T, L>(Cf + idx, cv);
+#pragma unroll
+                for (int q = 0; q < L; ++q) {
+                    cv[q] += d[q];
+                    bad |= !isfinite(cv[q]);
+                }
+                vst<T, L>(Cf + idx, cv);
+            } else {
+                vst<T, L>(a + idx, d);
+            }
+        }
+    }
+    if (UPDATE && bad) atomicOr(status, 1u);
+}
+
+// x-lines of 257..1024 cells, L lines per warp (FP32, nx a multiple of 4): the
+// warp's L lines sit in its shared buffer side by side, row i of lane chunk l
+// at l (M L + L) + i L, so one L-wide access serves all L lines in
+// warp_lines_solve_smv (lane l's access to row i lands in words
+// L (l (M + 1) + i) mod 32 + 0..L-1, distinct within each group of 32 / L
+// lanes served together).  Staging reads 16-byte vectors of each line and
+// writes L-wide rows (at most 2-way bank conflicts); the write-back is the
+// reverse.  Lines at or past nlines are solved on zeros and not stored.
+#ifndef CH_XSMV_MAX_BLOCKS
+#define CH_XSMV_MAX_BLOCKS 6
+#endif
+template <typename T, int M, int L, int W>
+struct XSmvShape {
+    static constexpr int kChunk = M * L + L;
+    static constexpr size_t kWarpBytes = (size_t)32 * kChunk * sizeof(T);
+    static constexpr int kFit = (int)((200 * 1024) / (W * kWarpBytes));
+    // and whose registers fit: about 80 a thread for L = 2, 120 for L = 4
+    static constexpr int kRegFit = 65536 / (W * 32 * (L <= 2 ? 80 : 120));
+    static constexpr int kCap = kRegFit < CH_XSMV_MAX_BLOCKS ? kRegFit : CH_XSMV_MAX_BLOCKS;
+    static constexpr int kMinBlocks = kFit < 1 ? 1 : (kFit > kCap ? kCap : kFit);
+};
+
+template <typename T, int M, int L, int W>
+__global__ void __launch_bounds__(W * 32, (XSmvShape<T, M, L, W>::kMinBlocks))
+ch_solve_x_smv(T* __restrict__ a, int64_t nlines, int nx, WCoef<T> cf) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_wait();
+    pdl_launch_dependents();
+    static_assert(sizeof(T) == 4 && M % 4 == 0, "FP32 rows in 16-byte vectors");
+    constexpr int kChunk = XSmvShape<T, M, L, W>::kChunk;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t line0 = ((int64_t)blockIdx.x * W + warp) * L;
+    if (line0 >= nlines) return;  // whole warp
+    T* sv = reinterpret_cast<T*>(smem_raw) + (size_t)warp * 32 * kChunk;
+    auto slot = [&](int e) { return (e / M) * kChunk + (e % M) * L; };
+    for (int e = lane * 4; e < 32 * M; e += 128) {
+        T t[L][4];
+#pragma unroll
+        for (int q = 0; q < L; ++q) {
+            if (e < nx && line0 + q < nlines) {
+                const float4 g = *reinterpret_cast<const float4*>(a + (line0 + q) * nx + e);
+                t[q][0] = g.x; t[q][1] = g.y; t[q][2] = g.z; t[q][3] = g.w;
+            } else {
+                t[q][0] = t[q][1] = t[q][2] = t[q][3] = T(0);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            T v[L];
+#pragma unroll
+            for (int q = 0; q < L; ++q) v[q] = t[q][k];
+            vst<T, L>(sv + slot(e + k), v);
+        }
+    }
+    __syncwarp();
+    warp_lines_solve_smv<T, M, L>(sv + (size_t)lane * kChunk, L, cf, lane);
+    __syncwarp();
+    for (int e = lane * 4; e < nx; e += 128) {
+        T t[L][4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            T v[L];
+            vld<T, L>(sv + slot(e + k), v);
+#pragma unroll
+            for (int q = 0; q < L; ++q) t[q][k] = v[q];
+        }
+#pragma unroll
+        for (int q = 0; q < L; ++q)
+            if (line0 + q < nlines)
+                *reinterpret_cast<float4*>(a + (line0 + q) * nx + e) = make_float4(t[q][0], t[q][1], t[q][2], t[q][3]);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1245,8 +1645,9 @@ ch_reduce_mass(const T* __restrict__ C, int nx, int64_t nrows, double* partials,
 // term in the field precision: one warp per x-row (k, j), lanes along x; the
 // forward neighbour wraps (periodic), is the cell itself (mirror ghost, zero
 // gradient at a no-flux wall) or its negation (Dirichlet ghost at the top
-// z-wall).
-template <typename T>
+// z-wall).  With MASS the same pass also sums C (block partials after the
+// energy partials), so both diagnostics cost one read of C.
+template <typename T, bool MASS = false>
 __global__ void __launch_bounds__(kRedThreads)
 ch_reduce_energy(const T* __restrict__ C, int nx, int ny, int nz, int bcx, int bcy, int bcz, T inv_h,
                  T half_cn2, double* partials, unsigned int* status) {
@@ -1255,7 +1656,7 @@ ch_reduce_energy(const T* __restrict__ C, int nx, int ny, int nz, int bcx, int b
     const int64_t nwarps = ((int64_t)gridDim.x * kRedThreads) >> 5;
     const int64_t nrows = (int64_t)ny * nz;
     const int64_t plane = (int64_t)nx * ny;
-    RedAcc<T> acc;
+    RedAcc<T> acc, macc;
     bool bad = false;
     for (int64_t row = warp0; row < nrows; row += nwarps) {
         const int j = (int)(row % ny), k = (int)(row / ny);
@@ -1288,9 +1689,11 @@ ch_reduce_energy(const T* __restrict__ C, int nx, int ny, int nz, int bcx, int b
                         const T gz = (zsign * zv[q] - c) * inv_h;
                         const T cc = c * (c - T(1));
                         acc.add(T(0.25) * cc * cc + half_cn2 * (gx * gx + gy * gy + gz * gz));
+                        if (MASS) macc.add(c);
                     }
                 }
                 acc.flush();
+                macc.flush();
                 continue;
             }
         }
@@ -1303,12 +1706,19 @@ ch_reduce_energy(const T* __restrict__ C, int nx, int ny, int nz, int bcx, int b
             const T gz = (zsign * pz[i] - c) * inv_h;
             const T cc = c * (c - T(1));
             acc.add(T(0.25) * cc * cc + half_cn2 * (gx * gx + gy * gy + gz * gz));
+            if (MASS) macc.add(c);
         }
         acc.flush();
+        macc.flush();
     }
     if (bad) atomicOr(status, 1u);
     const double v = block_sum(acc.total());
     if (threadIdx.x == 0) partials[blockIdx.x] = v;
+    if (MASS) {
+        __syncthreads();  // block_sum's shared slots are reused
+        const double m = block_sum(macc.total());
+        if (threadIdx.x == 0) partials[gridDim.x + blockIdx.x] = m;
+    }
 }
 
 static __global__ void __launch_bounds__(kRedThreads)

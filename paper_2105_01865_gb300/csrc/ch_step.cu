@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <tuple>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
@@ -43,6 +44,40 @@ constexpr size_t kMaxSmem = 227 * 1024;  // dynamic shared memory per CTA (sm_10
 // than in registers.
 #ifndef CH_X_SM
 #define CH_X_SM 1
+#endif
+// FP32 lines of 257..1024 cells: adjacent lines solved together per warp in
+// shared memory.  y and z: ch_solve_yz_v with CH_Y_LINES / CH_Z_LINES lines
+// per warp over tiles of CH_Y_COLS / CH_Z_COLS columns, at most
+// CH_Y_MAX_BLOCKS / CH_Z_MAX_BLOCKS CTAs per SM (lines = 1 keeps the one-line
+// tile solver; for z, CH_Z_TILE = 0 keeps the 2-CTA cluster column solver).
+// x: ch_solve_x_smv with CH_X_LINES lines per warp, CH_X_WARPS warps per CTA.
+// Defaults: the fastest measured on the 1024x1024x512 mesh.
+#ifndef CH_Y_LINES
+#define CH_Y_LINES 2
+#endif
+#ifndef CH_Y_COLS
+#define CH_Y_COLS 16
+#endif
+#ifndef CH_Y_MAX_BLOCKS
+#define CH_Y_MAX_BLOCKS 3
+#endif
+#ifndef CH_Z_TILE
+#define CH_Z_TILE 1
+#endif
+#ifndef CH_Z_LINES
+#define CH_Z_LINES 4
+#endif
+#ifndef CH_Z_COLS
+#define CH_Z_COLS 32
+#endif
+#ifndef CH_Z_MAX_BLOCKS
+#define CH_Z_MAX_BLOCKS 2
+#endif
+#ifndef CH_X_LINES
+#define CH_X_LINES 2
+#endif
+#ifndef CH_X_WARPS
+#define CH_X_WARPS 4
 #endif
 // Lines of 65..256 cells also over 2-CTA clusters (CTAs of 4 or 8 warps), so
 // that two tiles share an SM.
@@ -191,10 +226,61 @@ WCoef<T> wcoef(const LineTables& lt) {
 
 // Solve (I + c A_dir) x = a in place along direction dir for substep l's c;
 // for dir = 2 with Cupd != nullptr the solution is added to Cupd instead.
+// y (dir 1) or z (dir 2) lines through ch_solve_yz_v: L lines per warp,
+// NC-column tiles, at most B CTAs per SM.
+template <typename T, int M, int L, int NC, int B>
+void launch_yz_v(ch_handle* h, int dir, T* r, T* Cupd, const WCoef<T>& cf) {
+    using S = YZVShape<T, M, L, NC, B>;
+    const int nx = (int)h->n[0], ny = (int)h->n[1], nz = (int)h->n[2];
+    const unsigned xblocks = (unsigned)((nx + NC - 1) / NC);
+    const int64_t plane = (int64_t)nx * ny;
+    if (dir == 1)
+        launch_k(h->stream, ch_solve_yz_v<T, M, false, L, NC, B>, dim3(xblocks * (unsigned)nz), dim3(S::kWarps * 32),
+                 S::kTileBytes, r, nullptr, nx, plane, (int64_t)nx, cf, h->status);
+    else if (Cupd)
+        launch_k(h->stream, ch_solve_yz_v<T, M, true, L, NC, B>, dim3(xblocks * (unsigned)ny), dim3(S::kWarps * 32),
+                 S::kTileBytes, r, Cupd, nx, (int64_t)nx, plane, cf, h->status);
+    else
+        launch_k(h->stream, ch_solve_yz_v<T, M, false, L, NC, B>, dim3(xblocks * (unsigned)ny), dim3(S::kWarps * 32),
+                 S::kTileBytes, r, nullptr, nx, (int64_t)nx, plane, cf, h->status);
+}
+
+// Whether FP32 lines of 257..1024 cells (M = 16, 32) along dir go through the
+// multi-line shared-memory solvers (ch_solve_x_smv, ch_solve_yz_v).
+template <typename T, int M>
+bool multi_line(const ch_handle* h, int dir) {
+    if constexpr (sizeof(T) != 4 || M < 16) {
+        return false;
+    } else {
+        const int64_t nx = h->n[0];
+        if (dir == 0) return CH_X_LINES > 1 && nx % 4 == 0;
+        if (dir == 1) return CH_Y_LINES > 1 && nx % CH_Y_LINES == 0;
+        return CH_Z_TILE && CH_Z_LINES > 1 && nx % CH_Z_LINES == 0;
+    }
+}
+
 template <typename T, int M>
 int launch_solves_m(ch_handle* h, int l, int dir, T* r, T* Cupd, cudaEvent_t ev_after) {
     const int nx = (int)h->n[0], ny = (int)h->n[1], nz = (int)h->n[2];
     const WCoef<T> cf = wcoef<T>(h->lines[dir][l]);
+    if constexpr (sizeof(T) == 4 && M >= 16) {
+        if (multi_line<T, M>(h, dir)) {
+            if (dir == 0) {
+                constexpr int L = CH_X_LINES, W = CH_X_WARPS;
+                using S = XSmvShape<T, M, L, W>;
+                const int64_t nlines = (int64_t)ny * nz;
+                launch_k(h->stream, ch_solve_x_smv<T, M, L, W>, dim3((unsigned)((nlines + W * L - 1) / (W * L))),
+                         dim3(W * 32), W * S::kWarpBytes, r, nlines, nx, cf);
+            } else if (dir == 1) {
+                launch_yz_v<T, M, CH_Y_LINES, CH_Y_COLS, CH_Y_MAX_BLOCKS>(h, dir, r, Cupd, cf);
+            } else {
+                launch_yz_v<T, M, CH_Z_LINES, CH_Z_COLS, CH_Z_MAX_BLOCKS>(h, dir, r, Cupd, cf);
+            }
+            CHG_CUDA(h, cudaGetLastError());
+            if (ev_after) CHG_CUDA(h, cudaEventRecord(ev_after, h->stream));
+            return CH_OK;
+        }
+    }
     if (dir == 0) {
         const int64_t nlines = (int64_t)ny * nz;
         constexpr int wpb = 8, lpb = wpb * LinesPerWarp<T, M>::value;
@@ -410,8 +496,17 @@ int launch_cols(ch_handle* h, int l, int dir, T* r, T* Cupd) {
 }
 
 template <typename T>
+bool multi_line_any(const ch_handle* h, int l, int dir) {
+    switch (h->lines[dir][l].M) {
+        case 16: return multi_line<T, 16>(h, dir);
+        case 32: return multi_line<T, 32>(h, dir);
+        default: return false;
+    }
+}
+
+template <typename T>
 int launch_solve(ch_handle* h, int l, int dir, T* r, T* Cupd, cudaEvent_t ev_after) {
-    if (dir > 0) {
+    if (dir > 0 && !multi_line_any<T>(h, l, dir)) {
         const int rc = launch_cols<T>(h, l, dir, r, Cupd);
         if (rc >= 0) {
             if (rc == CH_OK && ev_after) CHG_CUDA(h, cudaEventRecord(ev_after, h->stream));
@@ -434,6 +529,19 @@ int set_attrs_m(ch_handle* h) {
     if constexpr (M >= 16)
         CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_x_sm<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(8 * XSmShape<T, M>::kWarpBytes)));
+    if constexpr (sizeof(T) == 4 && M >= 16) {
+        using SX = XSmvShape<T, M, CH_X_LINES, CH_X_WARPS>;
+        CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_x_smv<T, M, CH_X_LINES, CH_X_WARPS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(CH_X_WARPS * SX::kWarpBytes)));
+        using SY = YZVShape<T, M, CH_Y_LINES, CH_Y_COLS, CH_Y_MAX_BLOCKS>;
+        CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_yz_v<T, M, false, CH_Y_LINES, CH_Y_COLS, CH_Y_MAX_BLOCKS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SY::kTileBytes));
+        using SZ = YZVShape<T, M, CH_Z_LINES, CH_Z_COLS, CH_Z_MAX_BLOCKS>;
+        CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_yz_v<T, M, false, CH_Z_LINES, CH_Z_COLS, CH_Z_MAX_BLOCKS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SZ::kTileBytes));
+        CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_yz_v<T, M, true, CH_Z_LINES, CH_Z_COLS, CH_Z_MAX_BLOCKS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SZ::kTileBytes));
+    }
     const int shm = (int)YZShape<T, M>::kTileBytes;
     if ((size_t)shm > kMaxSmem) return CH_OK;  // never launched for this precision
     CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_yz<T, M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm));
@@ -483,21 +591,28 @@ int launch_explicit(ch_handle* h, int l, const T* C, const T* Hprev, T* Hout, T*
     const T* w = p.advect ? (const T*)h->vel[2] : nullptr;
     if (ev) CHG_CUDA(h, cudaEventRecord(ev[0], h->stream));
     if (nx % 2 == 0) {  // two cells per thread (paired FP32 arithmetic)
-        dim3 grid((nx + kTX2 - 1) / kTX2, (ny + kTY - 1) / kTY, (nz + kTZ2 - 1) / kTZ2);
+        const int tz = explicit_zchunk(nx, ny, nz, sizeof(T) == 4);
+        dim3 grid((nx + kTX2 - 1) / kTX2, (ny + kTY - 1) / kTY, (nz + tz - 1) / tz);
         dim3 block(32, kTY);
         const bool diri = p.bc[2] == CH_DIRICHLET;
-        if (p.advect && diri)
-            launch_k(h->stream, ch_explicit_rhs2<T, true, true>, dim3(grid), dim3(block), 0, C, u, v, w, Hprev, Hout, r,
-                     a);
-        else if (p.advect)
-            launch_k(h->stream, ch_explicit_rhs2<T, true, false>, dim3(grid), dim3(block), 0, C, u, v, w, Hprev, Hout,
-                     r, a);
-        else if (diri)
-            launch_k(h->stream, ch_explicit_rhs2<T, false, true>, dim3(grid), dim3(block), 0, C, u, v, w, Hprev, Hout,
-                     r, a);
-        else
-            launch_k(h->stream, ch_explicit_rhs2<T, false, false>, dim3(grid), dim3(block), 0, C, u, v, w, Hprev, Hout,
-                     r, a);
+        auto go = [&](auto tzc) {
+            constexpr int TZ = decltype(tzc)::value;
+            if (p.advect && diri)
+                launch_k(h->stream, ch_explicit_rhs2<T, true, true, TZ>, grid, block, 0, C, u, v, w, Hprev, Hout, r, a);
+            else if (p.advect)
+                launch_k(h->stream, ch_explicit_rhs2<T, true, false, TZ>, grid, block, 0, C, u, v, w, Hprev, Hout, r, a);
+            else if (diri)
+                launch_k(h->stream, ch_explicit_rhs2<T, false, true, TZ>, grid, block, 0, C, u, v, w, Hprev, Hout, r, a);
+            else
+                launch_k(h->stream, ch_explicit_rhs2<T, false, false, TZ>, grid, block, 0, C, u, v, w, Hprev, Hout, r,
+                         a);
+        };
+        if constexpr (sizeof(T) == 4) {
+            if (tz == kTZ2Deep) go(std::integral_constant<int, kTZ2Deep>{});
+            else go(std::integral_constant<int, kTZ2>{});
+        } else {
+            go(std::integral_constant<int, kTZ2>{});
+        }
     } else {
         dim3 grid((nx + kTX - 1) / kTX, (ny + kTY - 1) / kTY, (nz + kTZ - 1) / kTZ);
         dim3 block(kTX, kTY);
@@ -590,6 +705,23 @@ int launch_step(ch_handle* h) {
         if (rc != CH_OK) return rc;
     }
     return CH_OK;
+}
+
+// Both diagnostics in one pass over C: out[0] = mass, out[1] = free energy.
+template <typename T>
+int reduce_both(ch_handle* h, double* out) {
+    const ch_params& p = h->p;
+    ch_reduce_energy<T, true><<<h->red_blocks, kRedThreads, 0, h->stream>>>(
+        (const T*)h->C, (int)h->n[0], (int)h->n[1], (int)h->n[2], p.bc[0], p.bc[1], p.bc[2], (T)(1.0 / p.h),
+        (T)(0.5 * p.cn * p.cn), h->red_partials, h->status);
+    CHG_CUDA(h, cudaGetLastError());
+    const double h3 = p.h * p.h * p.h;
+    ch_reduce_finish<<<1, kRedThreads, 0, h->stream>>>(h->red_partials + h->red_blocks, h->red_blocks, h3, h->red_out);
+    CHG_CUDA(h, cudaGetLastError());
+    ch_reduce_finish<<<1, kRedThreads, 0, h->stream>>>(h->red_partials, h->red_blocks, h3, h->red_out + 1);
+    CHG_CUDA(h, cudaGetLastError());
+    CHG_CUDA(h, cudaMemcpyAsync(out, h->red_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return ch_sync(h);
 }
 
 template <typename T>
@@ -738,8 +870,8 @@ int ch_create(const ch_params* p, void* C, void* work, size_t work_bytes, void* 
     }
     if (rc == CH_OK) {
         h->red_blocks = 4 * 152;
-        if (cudaMalloc(&h->red_partials, (size_t)h->red_blocks * sizeof(double)) != cudaSuccess ||
-            cudaMalloc(&h->red_out, sizeof(double)) != cudaSuccess ||
+        if (cudaMalloc(&h->red_partials, 2 * (size_t)h->red_blocks * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&h->red_out, 2 * sizeof(double)) != cudaSuccess ||
             cudaMalloc(&h->status, sizeof(unsigned int)) != cudaSuccess)
             rc = CH_ENOMEM;
         else if (cudaMemset(h->status, 0, sizeof(unsigned int)) != cudaSuccess)
@@ -829,6 +961,16 @@ int ch_step(ch_handle* h, int64_t nsteps) {
 int ch_mass(ch_handle* h, double* out) {
     if (!h || !out) return CH_EINVAL;
     return h->prec == CH_F64 ? reduce<double>(h, false, out) : reduce<float>(h, false, out);
+}
+
+int ch_diagnostics(ch_handle* h, double* mass, double* free_energy) {
+    if (!h || !mass || !free_energy) return CH_EINVAL;
+    double out[2] = {0.0, 0.0};
+    const int rc = h->prec == CH_F64 ? reduce_both<double>(h, out) : reduce_both<float>(h, out);
+    if (rc != CH_OK) return rc;
+    *mass = out[0];
+    *free_energy = out[1];
+    return CH_OK;
 }
 
 int ch_free_energy(ch_handle* h, double* out) {

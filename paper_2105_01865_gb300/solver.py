@@ -115,6 +115,10 @@ class Solver:
     def free_energy(self):
         return capi.ch_free_energy(self.handle)
 
+    def diagnostics(self):
+        """(mass, free energy) in one pass over C."""
+        return capi.ch_diagnostics(self.handle)
+
     def sync(self):
         capi.ch_sync(self.handle)
 

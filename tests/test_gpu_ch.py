@@ -141,6 +141,29 @@ def test_fp64_mass_and_energy_reductions():
     assert abs(s.free_energy() - co.free_energy(C0, p)) <= 1e-12 * abs(co.free_energy(C0, p))
 
 
+@pytest.mark.parametrize("prec,shape", [("f64", (20, 18, 40)), ("f32", (20, 18, 40)), ("f32", (8, 6, 256))])
+def test_diagnostics_one_pass_matches_separate_reductions(prec, shape):
+    """ch_diagnostics (mass and free energy from one pass over C) against
+    ch_mass, ch_free_energy and the oracle, on the same values: walls in y
+    and z, periodic x; the (8, 6, 256) shape takes the FP32 16-byte path."""
+    h = 1.0 / 20
+    bc = (co.PERIODIC, co.NOFLUX, co.NOFLUX)
+    cn = 0.75 * h
+    rng = np.random.default_rng(3)
+    C0 = 0.5 + 0.3 * rng.standard_normal(shape)
+    if prec == "f32":
+        C0 = C0.astype(np.float32).astype(np.float64)
+    s = make(shape, h, bc, cn, 100.0, 1e-3, C0, prec)
+    m, e = s.diagnostics()
+    p = oracle_params(shape, h, bc, cn, 100.0, 1e-3)
+    assert abs(m - s.mass()) <= 1e-12 * abs(m)
+    assert abs(m - co.mass(C0, p)) <= 1e-12 * abs(m)
+    # FP32 forms the energy terms in FP32 (each within a few roundings)
+    etol = 1e-12 if prec == "f64" else 1e-6
+    assert abs(e - s.free_energy()) <= 1e-12 * abs(e)
+    assert abs(e - co.free_energy(C0, p)) <= etol * abs(e)
+
+
 def test_fp64_mass_conserved_with_flow():
     shape, h = (32, 24, 40), 1.0 / 32
     bc = (co.PERIODIC, co.PERIODIC, co.NOFLUX)
@@ -388,3 +411,23 @@ def test_fp32_error_per_field_and_step_count(case, hbar):
         assert_parity(s.field(), Cr, 1e-5, f"{case} FP32, {n} steps, C")
         assert_parity(H2, H2r, hbar, f"{case} FP32, {n} steps, H of substep 2")
         assert_parity(H3, H3r, hbar, f"{case} FP32, {n} steps, H of substep 3")
+
+
+def test_deep_explicit_tiles_ragged_z_fp32_against_fp64():
+    """The 512 x 512 x 120 shear drop: enough CTAs that the FP32 explicit
+    kernel marches 16-plane tiles (at least 8 waves on the device), the last
+    one 8 planes deep; the FP64 path marches 10-plane tiles and is pinned to
+    the oracle on the smaller cases.  Relative L2 and element bars on C after
+    2 steps, and mass conservation."""
+    f = inputs.shear_drop_box(512, 512, 120)
+    h = f["h"]
+    dt = min(0.9 * stability.stable_dt(f["shape"], h, f["bc"], f["cn"], f["pe"]), 0.5 * h / 0.5)
+    S = {p: make(f["shape"], h, f["bc"], f["cn"], f["pe"], dt, f["C"], p, vel=f["vel"]) for p in ("f32", "f64")}
+    m0 = {p: s.mass() for p, s in S.items()}
+    for s in S.values():
+        s.step(2)
+        s.sync()
+    assert_parity(S["f32"].field(), S["f64"].field(), 1e-6, "512x512x120 shear drop, FP32 (16-plane tiles) vs FP64")
+    for p, s in S.items():
+        assert abs(s.mass() - m0[p]) <= (1e-6 if p == "f32" else 1e-12) * abs(m0[p])
+        s.close()
