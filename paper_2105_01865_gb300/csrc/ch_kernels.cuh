@@ -1299,7 +1299,7 @@ ch_solve_yz_v(T* __restrict__ a, T* __restrict__ Cf, int nx, int64_t outer_strid
 // writes L-wide rows (at most 2-way bank conflicts); the write-back is the
 // reverse.  Lines at or past nlines are solved on zeros and not stored.
 #ifndef CH_XSMV_MAX_BLOCKS
-#define CH_XSMV_MAX_BLOCKS 6
+#define CH_XSMV_MAX_BLOCKS 12
 #endif
 template <typename T, int M, int L, int W>
 struct XSmvShape {

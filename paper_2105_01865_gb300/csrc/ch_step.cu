@@ -53,13 +53,13 @@ constexpr size_t kMaxSmem = 227 * 1024;  // dynamic shared memory per CTA (sm_10
 // x: ch_solve_x_smv with CH_X_LINES lines per warp, CH_X_WARPS warps per CTA.
 // Defaults: the fastest measured on the 1024x1024x512 mesh.
 #ifndef CH_Y_LINES
-#define CH_Y_LINES 2
+#define CH_Y_LINES 4
 #endif
 #ifndef CH_Y_COLS
-#define CH_Y_COLS 16
+#define CH_Y_COLS 32
 #endif
 #ifndef CH_Y_MAX_BLOCKS
-#define CH_Y_MAX_BLOCKS 3
+#define CH_Y_MAX_BLOCKS 2
 #endif
 #ifndef CH_Z_TILE
 #define CH_Z_TILE 1
@@ -77,7 +77,11 @@ constexpr size_t kMaxSmem = 227 * 1024;  // dynamic shared memory per CTA (sm_10
 #define CH_X_LINES 2
 #endif
 #ifndef CH_X_WARPS
-#define CH_X_WARPS 4
+#define CH_X_WARPS 2
+#endif
+// shortest lines (in rows per lane, M) that take the multi-line solvers
+#ifndef CH_MULTI_MIN_M
+#define CH_MULTI_MIN_M 16
 #endif
 // Lines of 65..256 cells also over 2-CTA clusters (CTAs of 4 or 8 warps), so
 // that two tiles share an SM.
@@ -249,7 +253,7 @@ void launch_yz_v(ch_handle* h, int dir, T* r, T* Cupd, const WCoef<T>& cf) {
 // multi-line shared-memory solvers (ch_solve_x_smv, ch_solve_yz_v).
 template <typename T, int M>
 bool multi_line(const ch_handle* h, int dir) {
-    if constexpr (sizeof(T) != 4 || M < 16) {
+    if constexpr (sizeof(T) != 4 || M < CH_MULTI_MIN_M || M < 4) {
         return false;
     } else {
         const int64_t nx = h->n[0];
@@ -263,7 +267,7 @@ template <typename T, int M>
 int launch_solves_m(ch_handle* h, int l, int dir, T* r, T* Cupd, cudaEvent_t ev_after) {
     const int nx = (int)h->n[0], ny = (int)h->n[1], nz = (int)h->n[2];
     const WCoef<T> cf = wcoef<T>(h->lines[dir][l]);
-    if constexpr (sizeof(T) == 4 && M >= 16) {
+    if constexpr (sizeof(T) == 4 && M >= CH_MULTI_MIN_M && M >= 4) {
         if (multi_line<T, M>(h, dir)) {
             if (dir == 0) {
                 constexpr int L = CH_X_LINES, W = CH_X_WARPS;
@@ -498,6 +502,8 @@ int launch_cols(ch_handle* h, int l, int dir, T* r, T* Cupd) {
 template <typename T>
 bool multi_line_any(const ch_handle* h, int l, int dir) {
     switch (h->lines[dir][l].M) {
+        case 4: return multi_line<T, 4>(h, dir);
+        case 8: return multi_line<T, 8>(h, dir);
         case 16: return multi_line<T, 16>(h, dir);
         case 32: return multi_line<T, 32>(h, dir);
         default: return false;
@@ -529,7 +535,7 @@ int set_attrs_m(ch_handle* h) {
     if constexpr (M >= 16)
         CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_x_sm<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(8 * XSmShape<T, M>::kWarpBytes)));
-    if constexpr (sizeof(T) == 4 && M >= 16) {
+    if constexpr (sizeof(T) == 4 && M >= CH_MULTI_MIN_M && M >= 4) {
         using SX = XSmvShape<T, M, CH_X_LINES, CH_X_WARPS>;
         CHG_CUDA(h, cudaFuncSetAttribute(ch_solve_x_smv<T, M, CH_X_LINES, CH_X_WARPS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(CH_X_WARPS * SX::kWarpBytes)));
