@@ -1267,23 +1267,41 @@ ch_solve_yz_v(T* __restrict__ a, T* __restrict__ Cf, int nx, int64_t outer_strid
     warp_lines_solve_smv<T, M, L>(s + (size_t)lane * kChunk + warp * L, NC, cf, lane);
     __syncthreads();
     bool bad = false;
-#pragma unroll 4
-    for (int j = rr; j < n; j += 32) {
-        if (c < nl) {
-            const int64_t idx = base + (int64_t)j * line_stride + c;
-            T d[L];
-            vld<T, L>(s + slot(j), d);
-            if (UPDATE) {
-                T cv[L];
-                vld<T, L>(Cf + idx, cv);
+    if constexpr (UPDATE) {
+        // rows rr + 32 t (t < M) in batches of 8: the batch's C loads are all
+        // issued before its first store (a store to C would otherwise hold
+        // back the next row's load)
+        constexpr int kB = M < 8 ? M : 8;
+#pragma unroll 1
+        for (int t0 = 0; t0 < M; t0 += kB) {
+            T cv[kB][L];
 #pragma unroll
-                for (int q = 0; q < L; ++q) {
-                    cv[q] += d[q];
-                    bad |= !isfinite(cv[q]);
+            for (int t = 0; t < kB; ++t) {
+                const int j = rr + 32 * (t0 + t);
+                if (j < n && c < nl) vld<T, L>(Cf + base + (int64_t)j * line_stride + c, cv[t]);
+            }
+#pragma unroll
+            for (int t = 0; t < kB; ++t) {
+                const int j = rr + 32 * (t0 + t);
+                if (j < n && c < nl) {
+                    T d[L];
+                    vld<T, L>(s + slot(j), d);
+#pragma unroll
+                    for (int q = 0; q < L; ++q) {
+                        cv[t][q] += d[q];
+                        bad |= !isfinite(cv[t][q]);
+                    }
+                    vst<T, L>(Cf + base + (int64_t)j * line_stride + c, cv[t]);
                 }
-                vst<T, L>(Cf + idx, cv);
-            } else {
-                vst<T, L>(a + idx, d);
+            }
+        }
+    } else {
+#pragma unroll 4
+        for (int j = rr; j < n; j += 32) {
+            if (c < nl) {
+                T d[L];
+                vld<T, L>(s + slot(j), d);
+                vst<T, L>(a + base + (int64_t)j * line_stride + c, d);
             }
         }
     }
@@ -1325,23 +1343,35 @@ ch_solve_x_smv(T* __restrict__ a, int64_t nlines, int nx, WCoef<T> cf) {
     if (line0 >= nlines) return;  // whole warp
     T* sv = reinterpret_cast<T*>(smem_raw) + (size_t)warp * 32 * kChunk;
     auto slot = [&](int e) { return (e / M) * kChunk + (e % M) * L; };
-    for (int e = lane * 4; e < 32 * M; e += 128) {
-        T t[L][4];
+    // the lane's M / 4 vectors of each line, all loads issued before the
+    // first shared store (batches of 4 vectors per line)
+    constexpr int kNV = M / 4, kB = kNV < 4 ? kNV : 4;
 #pragma unroll
-        for (int q = 0; q < L; ++q) {
-            if (e < nx && line0 + q < nlines) {
-                const float4 g = *reinterpret_cast<const float4*>(a + (line0 + q) * nx + e);
-                t[q][0] = g.x; t[q][1] = g.y; t[q][2] = g.z; t[q][3] = g.w;
-            } else {
-                t[q][0] = t[q][1] = t[q][2] = t[q][3] = T(0);
+    for (int v0 = 0; v0 < kNV; v0 += kB) {
+        T t[kB][L][4];
+#pragma unroll
+        for (int b = 0; b < kB; ++b) {
+            const int e = lane * 4 + 128 * (v0 + b);
+#pragma unroll
+            for (int q = 0; q < L; ++q) {
+                if (e < nx && line0 + q < nlines) {
+                    const float4 g = *reinterpret_cast<const float4*>(a + (line0 + q) * nx + e);
+                    t[b][q][0] = g.x; t[b][q][1] = g.y; t[b][q][2] = g.z; t[b][q][3] = g.w;
+                } else {
+                    t[b][q][0] = t[b][q][1] = t[b][q][2] = t[b][q][3] = T(0);
+                }
             }
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            T v[L];
+        for (int b = 0; b < kB; ++b) {
+            const int e = lane * 4 + 128 * (v0 + b);
 #pragma unroll
-            for (int q = 0; q < L; ++q) v[q] = t[q][k];
-            vst<T, L>(sv + slot(e + k), v);
+            for (int k = 0; k < 4; ++k) {
+                T v[L];
+#pragma unroll
+                for (int q = 0; q < L; ++q) v[q] = t[b][q][k];
+                vst<T, L>(sv + slot(e + k), v);
+            }
         }
     }
     __syncwarp();
