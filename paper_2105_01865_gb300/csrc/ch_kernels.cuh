@@ -1029,20 +1029,40 @@ __device__ __forceinline__ void cp_async_vec(T* smem, const T* gmem) {
 // the scans' span matrices are shared by the L lines.  Each line's arithmetic
 // is that of warp_line_solve_sm, in the same order, so the results agree with
 // it bit for bit.
+// CH_SMV_TABLE = 1: the LU factors of every row come from the tables (one
+// L1-resident load per row, shared by the L lines) instead of register
+// constants on the interior rows; the periodic correction still skips the
+// interior rows.
+#ifndef CH_SMV_TABLE
+#define CH_SMV_TABLE 0
+#endif
+// rows per unrolled step of the solver's passes
+#ifndef CH_SMV_UNROLL
+#define CH_SMV_UNROLL 8
+#endif
+constexpr int kSmvUnroll = CH_SMV_UNROLL;
 template <typename T, int M, int L>
 __device__ __forceinline__ void warp_lines_solve_smv(T* p, int stride, const WCoef<T>& cf, int lane) {
     const bool per = cf.periodic;
     const int lo = cf.r0 - lane * M, hi = cf.r1 - lane * M;  // this chunk's interior rows: [lo, hi)
     auto inner = [&](int i) { return i >= lo && i < hi; };
     auto fwd = [&](int i) {
-        V4<T> c = {cf.k[0], cf.k[1], cf.k[2], T(0)};
-        if (!inner(i)) c = ld4(cf.fwd + (i * 32 + lane) * 4);
-        return c;
+        if constexpr (CH_SMV_TABLE) {
+            return ld4(cf.fwd + (i * 32 + lane) * 4);
+        } else {
+            V4<T> c = {cf.k[0], cf.k[1], cf.k[2], T(0)};
+            if (!inner(i)) c = ld4(cf.fwd + (i * 32 + lane) * 4);
+            return c;
+        }
     };
     auto bwd = [&](int i, T& u1, T& u2) {
-        u1 = cf.k[3];
-        u2 = cf.k[4];
-        if (!inner(i)) ld2(cf.bwd + (i * 32 + lane) * 2, u1, u2);
+        if constexpr (CH_SMV_TABLE) {
+            ld2(cf.bwd + (i * 32 + lane) * 2, u1, u2);
+        } else {
+            u1 = cf.k[3];
+            u2 = cf.k[4];
+            if (!inner(i)) ld2(cf.bwd + (i * 32 + lane) * 2, u1, u2);
+        }
     };
     // ---- forward elimination: zero-start pass over the chunk
     T y1[L], y2[L], acc[L][4];
@@ -1051,7 +1071,7 @@ __device__ __forceinline__ void warp_lines_solve_smv(T* p, int stride, const WCo
         y1[q] = y2[q] = T(0);
         acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = T(0);
     }
-#pragma unroll 8
+#pragma unroll kSmvUnroll
     for (int i = 0; i < M; ++i) {
         const V4<T> c = fwd(i);
         T vi[L];
@@ -1104,7 +1124,7 @@ __device__ __forceinline__ void warp_lines_solve_smv(T* p, int stride, const WCo
         y2[q] = __shfl_up_sync(kFull, q1[q], 1);
         if (lane == 0) y1[q] = y2[q] = T(0);
     }
-#pragma unroll 8
+#pragma unroll kSmvUnroll
     for (int i = 0; i < M; ++i) {
         const V4<T> c = fwd(i);
         T vi[L];
@@ -1142,7 +1162,7 @@ __device__ __forceinline__ void warp_lines_solve_smv(T* p, int stride, const WCo
     T x1[L], x2[L];
 #pragma unroll
     for (int q = 0; q < L; ++q) x1[q] = x2[q] = T(0);
-#pragma unroll 8
+#pragma unroll kSmvUnroll
     for (int i = M - 1; i >= 0; --i) {
         T u1, u2;
         bwd(i, u1, u2);
@@ -1185,7 +1205,7 @@ __device__ __forceinline__ void warp_lines_solve_smv(T* p, int stride, const WCo
         x2[q] = __shfl_down_sync(kFull, q1[q], 1);
         if (lane == 31) x1[q] = x2[q] = T(0);
     }
-#pragma unroll 8
+#pragma unroll kSmvUnroll
     for (int i = M - 1; i >= 0; --i) {
         T u1, u2;
         bwd(i, u1, u2);
@@ -1698,6 +1718,12 @@ ch_reduce_energy(const T* __restrict__ C, int nx, int ny, int nz, int bcx, int b
         const T* pz = C + (int64_t)kp * plane + (int64_t)j * nx;
         if constexpr (sizeof(T) == 4) {
             if (nx % 128 == 0) {  // 4 consecutive cells per lane, 16-byte loads (rows are 512-byte multiples)
+                // the lane's 4 energy terms are summed plainly (no
+                // cancellation: every term is non-negative; 3 roundings of
+                // relative size 2^-24) and the sum enters the compensated
+                // accumulator once; the mass adds every C compensated, as
+                // ch_reduce_mass does
+#pragma unroll 2
                 for (int i0 = 4 * lane; i0 < nx; i0 += 128) {
                     const float4 c4 = *reinterpret_cast<const float4*>(p + i0);
                     const float4 y4 = *reinterpret_cast<const float4*>(py + i0);
@@ -1710,6 +1736,7 @@ ch_reduce_energy(const T* __restrict__ C, int nx, int ny, int nz, int bcx, int b
                     }
                     const float cv[4] = {c4.x, c4.y, c4.z, c4.w}, xv[4] = {c4.y, c4.z, c4.w, xn};
                     const float yv[4] = {y4.x, y4.y, y4.z, y4.w}, zv[4] = {z4.x, z4.y, z4.z, z4.w};
+                    float e4 = 0.f;
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const T c = cv[q];
@@ -1718,9 +1745,10 @@ ch_reduce_energy(const T* __restrict__ C, int nx, int ny, int nz, int bcx, int b
                         const T gy = (yv[q] - c) * inv_h;
                         const T gz = (zsign * zv[q] - c) * inv_h;
                         const T cc = c * (c - T(1));
-                        acc.add(T(0.25) * cc * cc + half_cn2 * (gx * gx + gy * gy + gz * gz));
+                        e4 += T(0.25) * cc * cc + half_cn2 * (gx * gx + gy * gy + gz * gz);
                         if (MASS) macc.add(c);
                     }
+                    acc.add(e4);
                 }
                 acc.flush();
                 macc.flush();

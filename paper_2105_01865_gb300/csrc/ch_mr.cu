@@ -218,39 +218,88 @@ struct BlockSum {
 // gradient is the 4-point x-stencil of g; a lane sums its 4 terms, a warp
 // scan of the lane sums gives the chunk's prefix, and a compensated carry
 // joins the chunks (R20).  u(face i) = u_ref(j, k) + h sum_{i' < i} Gx(i').
+//
+// The 8 warps of a CTA take 8 consecutive j of one k, whose y-stencils start
+// within a few coarse rows of each other.  When they all start within
+// qrows - 4 rows of the first (qrows > 0), the CTA first contracts the 4
+// coarse z-rows once for each of those y-rows into shared memory,
+// Q(r, ix) = sum_c wz_c G(ix, sy0 + r, sz + c), and each warp then forms
+// g(ix) = sum_b wy_b Q(sy - sy0 + b, ix): about 6 instead of 32 coarse-row
+// reads per ix per CTA.  Otherwise each warp contracts its 16 rows itself.
 constexpr int kMrWarps = 8;
+constexpr int kMrQRows = 8;
+constexpr size_t kMrMaxSmem = 226 * 1024;  // dynamic shared memory per CTA (227 KB on sm_103a, less the static)
 
 template <typename T>
 __global__ void __launch_bounds__(kMrWarps * 32, 4)
 mr_integrate_x(const T* __restrict__ gx, const T* __restrict__ uc, Tab<T> tx, Tab<T> ty, Tab<T> tz, MrArgs a,
-               T* __restrict__ u) {
-    extern __shared__ __align__(16) unsigned char mr_smem[];  // kMrWarps coarse lines of ncx + 3 values
+               T* __restrict__ u, int qrows) {
+    // kMrWarps coarse lines of ncx + 4 values, then qrows rows of Q
+    extern __shared__ __align__(16) unsigned char mr_smem[];
+    __shared__ int dmax;
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nlines = a.ny * a.nz;
     const int warp = blockIdx.x * kMrWarps + wib;
-    if (warp >= a.ny * a.nz) return;  // whole warp
-    const int j = warp % a.ny, k = warp / a.ny;
+    const bool live = warp < nlines;
+    const int wl = live ? warp : nlines - 1;  // a warp past the last line stands in for it until it leaves
+    const int j = wl % a.ny, k = wl / a.ny;
     T wy[4], wz[4];
     load_w(ty.w, j, wy);
     load_w(tz.w, k, wz);
     const int sy = ty.s[j], sz = tz.s[k];
+    const int ld = a.ncx + 4;
     // the coarse line, followed by copies of its first 3 values, so a stencil
     // starting at sx <= ncx - 1 reads g[sx .. sx + 3] without wrapping
-    T* g = reinterpret_cast<T*>(mr_smem) + (int64_t)wib * (a.ncx + 4);
-    int rows[4][4];  // element offsets of the 16 coarse rows (the coarse mesh has < 2^31 cells)
+    T* g = reinterpret_cast<T*>(mr_smem) + (int64_t)wib * ld;
+    const int w0 = blockIdx.x * kMrWarps, wlast = min(w0 + kMrWarps - 1, nlines - 1);
+    const int sy0 = ty.s[w0 % a.ny];
+    const int d = sy >= sy0 ? sy - sy0 : sy - sy0 + a.ncy;  // this line's first y-row, counted from sy0
+    bool shared_q = false;
+    if (qrows > 0 && w0 / a.ny == wlast / a.ny) {  // one k (and so one sz, wz) for the whole CTA
+        if (threadIdx.x == 0) dmax = 0;
+        __syncthreads();
+        if (lane == 0) atomicMax(&dmax, d);
+        __syncthreads();
+        shared_q = dmax + 4 <= qrows;
+    }
+    if (shared_q) {
+        const int nq = dmax + 4;
+        T* Q = reinterpret_cast<T*>(mr_smem) + (int64_t)kMrWarps * ld;
+        for (int r = 0; r < nq; ++r) {
+            const int ky = (sy0 + r) % a.ncy;
+            int zr[4];
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) rows[c][b] = (wrap_add(sz, c, a.ncz) * a.ncy + wrap_add(sy, b, a.ncy)) * a.ncx;
-    for (int ix = lane; ix < a.ncx + 3; ix += 32) {
-        const int cx = ix < a.ncx ? ix : ix - a.ncx;
-        T acc = T(0);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const T accy = wy[0] * gx[rows[c][0] + cx] + wy[1] * gx[rows[c][1] + cx] + wy[2] * gx[rows[c][2] + cx] +
-                           wy[3] * gx[rows[c][3] + cx];
-            acc += wz[c] * accy;
+            for (int c = 0; c < 4; ++c) zr[c] = (wrap_add(sz, c, a.ncz) * a.ncy + ky) * a.ncx;
+            for (int ix = threadIdx.x; ix < a.ncx + 3; ix += kMrWarps * 32) {
+                const int cx = ix < a.ncx ? ix : ix - a.ncx;
+                Q[r * ld + ix] = wz[0] * gx[zr[0] + cx] + wz[1] * gx[zr[1] + cx] + wz[2] * gx[zr[2] + cx] +
+                                 wz[3] * gx[zr[3] + cx];
+            }
         }
-        g[ix] = acc;
+        __syncthreads();
+        if (!live) return;  // whole warp
+        const T* q0 = Q + d * ld;
+        for (int ix = lane; ix < a.ncx + 3; ix += 32)
+            g[ix] = wy[0] * q0[ix] + wy[1] * q0[ld + ix] + wy[2] * q0[2 * ld + ix] + wy[3] * q0[3 * ld + ix];
+    } else {
+        if (!live) return;  // whole warp
+        int rows[4][4];  // element offsets of the 16 coarse rows (the coarse mesh has < 2^31 cells)
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                rows[c][b] = (wrap_add(sz, c, a.ncz) * a.ncy + wrap_add(sy, b, a.ncy)) * a.ncx;
+        for (int ix = lane; ix < a.ncx + 3; ix += 32) {
+            const int cx = ix < a.ncx ? ix : ix - a.ncx;
+            T acc = T(0);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const T accy = wy[0] * gx[rows[c][0] + cx] + wy[1] * gx[rows[c][1] + cx] +
+                               wy[2] * gx[rows[c][2] + cx] + wy[3] * gx[rows[c][3] + cx];
+                acc += wz[c] * accy;
+            }
+            g[ix] = acc;
+        }
     }
     T uref = T(0);
     if (!a.wall[0]) uref = hermite2(uc, (int64_t)a.ncy * a.ncfx, (int64_t)a.ncfx, a.ncz, a.ncy, sz, wz, sy, wy);
@@ -464,15 +513,18 @@ int interp(ch_handle* h, cudaEvent_t* ev = nullptr) {
     {
         const int64_t warps = (int64_t)a.ny * a.nz;
         const unsigned blocks = (unsigned)((warps + kMrWarps - 1) / kMrWarps);
-        const size_t smem = (size_t)kMrWarps * (a.ncx + 4) * sizeof(T);
+        // the shared z-contraction's rows where they fit beside the warps' lines
+        const size_t line_bytes = (size_t)(a.ncx + 4) * sizeof(T);
+        const int qrows = (kMrWarps + kMrQRows) * line_bytes <= kMrMaxSmem ? kMrQRows : 0;
+        const size_t smem = (kMrWarps + qrows) * line_bytes;
         static bool attr_set = false;  // one instantiation per T
         if (!attr_set) {
-            CHG_CUDA(h, cudaFuncSetAttribute(mr_integrate_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(kMrWarps * (kMaxCoarseLine + 4) * sizeof(T))));
+            const size_t most = std::min((size_t)(kMrWarps + kMrQRows) * (kMaxCoarseLine + 4) * sizeof(T), kMrMaxSmem);
+            CHG_CUDA(h, cudaFuncSetAttribute(mr_integrate_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most));
             attr_set = true;
         }
         mr_integrate_x<T><<<blocks, kMrWarps * 32, smem, h->stream>>>((const T*)h->grad_c[0], (const T*)h->vel_c[0],
-                                                                      tx, ty, tz, a, (T*)h->vel[0]);
+                                                                      tx, ty, tz, a, (T*)h->vel[0], qrows);
         CHG_CUDA(h, cudaGetLastError());
         if (ev) CHG_CUDA(h, cudaEventRecord(ev[2], h->stream));
     }
