@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "ch_internal.h"
@@ -228,6 +229,10 @@ struct BlockSum {
 // reads per ix per CTA.  Otherwise each warp contracts its 16 rows itself.
 constexpr int kMrWarps = 8;
 constexpr int kMrQRows = 8;
+// adjacent fine columns per thread of the y/z line march (1, 2 or 4)
+#ifndef CH_MR_CPT
+#define CH_MR_CPT 4
+#endif
 constexpr size_t kMrMaxSmem = 226 * 1024;  // dynamic shared memory per CTA (227 KB on sm_103a, less the static)
 
 template <typename T>
@@ -248,8 +253,8 @@ mr_integrate_x(const T* __restrict__ gx, const T* __restrict__ uc, Tab<T> tx, Ta
     load_w(tz.w, k, wz);
     const int sy = ty.s[j], sz = tz.s[k];
     const int ld = a.ncx + 4;
-    // the coarse line, followed by copies of its first 3 values, so a stencil
-    // starting at sx <= ncx - 1 reads g[sx .. sx + 3] without wrapping
+    // the coarse line, followed by copies of its first 4 values, so a stencil
+    // starting at sx <= ncx - 1 reads g[sx .. sx + 4] without wrapping
     T* g = reinterpret_cast<T*>(mr_smem) + (int64_t)wib * ld;
     const int w0 = blockIdx.x * kMrWarps, wlast = min(w0 + kMrWarps - 1, nlines - 1);
     const int sy0 = ty.s[w0 % a.ny];
@@ -270,7 +275,7 @@ mr_integrate_x(const T* __restrict__ gx, const T* __restrict__ uc, Tab<T> tx, Ta
             int zr[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) zr[c] = (wrap_add(sz, c, a.ncz) * a.ncy + ky) * a.ncx;
-            for (int ix = threadIdx.x; ix < a.ncx + 3; ix += kMrWarps * 32) {
+            for (int ix = threadIdx.x; ix < a.ncx + 4; ix += kMrWarps * 32) {
                 const int cx = ix < a.ncx ? ix : ix - a.ncx;
                 Q[r * ld + ix] = wz[0] * gx[zr[0] + cx] + wz[1] * gx[zr[1] + cx] + wz[2] * gx[zr[2] + cx] +
                                  wz[3] * gx[zr[3] + cx];
@@ -279,7 +284,7 @@ mr_integrate_x(const T* __restrict__ gx, const T* __restrict__ uc, Tab<T> tx, Ta
         __syncthreads();
         if (!live) return;  // whole warp
         const T* q0 = Q + d * ld;
-        for (int ix = lane; ix < a.ncx + 3; ix += 32)
+        for (int ix = lane; ix < a.ncx + 4; ix += 32)
             g[ix] = wy[0] * q0[ix] + wy[1] * q0[ld + ix] + wy[2] * q0[2 * ld + ix] + wy[3] * q0[3 * ld + ix];
     } else {
         if (!live) return;  // whole warp
@@ -289,7 +294,7 @@ mr_integrate_x(const T* __restrict__ gx, const T* __restrict__ uc, Tab<T> tx, Ta
 #pragma unroll
             for (int b = 0; b < 4; ++b)
                 rows[c][b] = (wrap_add(sz, c, a.ncz) * a.ncy + wrap_add(sy, b, a.ncy)) * a.ncx;
-        for (int ix = lane; ix < a.ncx + 3; ix += 32) {
+        for (int ix = lane; ix < a.ncx + 4; ix += 32) {
             const int cx = ix < a.ncx ? ix : ix - a.ncx;
             T acc = T(0);
 #pragma unroll
@@ -319,15 +324,32 @@ mr_integrate_x(const T* __restrict__ gx, const T* __restrict__ uc, Tab<T> tx, Ta
 #pragma unroll
             for (int q = 0; q < 4; ++q) sxq[q] = ib + q < a.nx ? tx.s[ib + q] : 0;
         }
+        int span = sxq[3] - sxq[0];  // the starts are non-decreasing modulo ncx
+        if (span < 0) span += a.ncx;
+        if (ib + 3 < a.nx && span <= 1) {
+            // the 4 cells' stencils start at s0 or s0 + 1 modulo ncx (a coarse
+            // mesh at least twice as coarse as the fine one): 5 shared loads
+            // serve them, instead of 16 (g[s0 + 1 + m] is g[m] past the wrap)
+            const T* gs = g + sxq[0];
+            const T g0 = gs[0], g1 = gs[1], g2 = gs[2], g3 = gs[3], g4 = gs[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int i = ib + q;
-            gv[q] = T(0);
-            if (i < a.nx) {
+            for (int q = 0; q < 4; ++q) {
                 T wx[4];
-                load_w(tx.w, i, wx);
-                const T* gs = g + sxq[q];
-                gv[q] = wx[0] * gs[0] + wx[1] * gs[1] + wx[2] * gs[2] + wx[3] * gs[3];
+                load_w(tx.w, ib + q, wx);
+                const bool o = sxq[q] != sxq[0];
+                gv[q] = wx[0] * (o ? g1 : g0) + wx[1] * (o ? g2 : g1) + wx[2] * (o ? g3 : g2) + wx[3] * (o ? g4 : g3);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int i = ib + q;
+                gv[q] = T(0);
+                if (i < a.nx) {
+                    T wx[4];
+                    load_w(tx.w, i, wx);
+                    const T* gs = g + sxq[q];
+                    gv[q] = wx[0] * gs[0] + wx[1] * gs[1] + wx[2] * gs[2] + wx[3] * gs[3];
+                }
             }
         }
         const T l1 = gv[0], l2 = l1 + gv[1], l3 = l2 + gv[2], tot = l3 + gv[3];
@@ -411,15 +433,58 @@ mr_plane_yz(const T* __restrict__ G, Tab<T> tx, Tab<T> ty, Tab<T> tz, MrArgs a, 
 // at the coarse nodes of the current stencil sit in a window that slides with
 // it (one coalesced load per coarse node passed), so a fine cell costs its
 // 4-point stencil along the line, the running sum and one store.
-template <typename T, int DIR>
+// CPT adjacent columns i .. i + CPT - 1 per thread (nx a multiple of CPT):
+// the loads of the start and weights along the line, the window test and the
+// loop serve all CPT columns, and the window loads and stores move CPT values
+// at once.
+template <typename T, int CPT>
+struct MrVec;
+template <typename T>
+struct MrVec<T, 1> {
+    static __device__ __forceinline__ void ld(const T* p, T* v) { v[0] = *p; }
+    static __device__ __forceinline__ void st(T* p, const T* v) { *p = v[0]; }
+};
+template <>
+struct MrVec<float, 2> {
+    static __device__ __forceinline__ void ld(const float* p, float* v) {
+        const float2 t = *reinterpret_cast<const float2*>(p);
+        v[0] = t.x; v[1] = t.y;
+    }
+    static __device__ __forceinline__ void st(float* p, const float* v) {
+        *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+    }
+};
+template <>
+struct MrVec<float, 4> {
+    static __device__ __forceinline__ void ld(const float* p, float* v) {
+        const float4 t = *reinterpret_cast<const float4*>(p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+    static __device__ __forceinline__ void st(float* p, const float* v) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+template <>
+struct MrVec<double, 2> {
+    static __device__ __forceinline__ void ld(const double* p, double* v) {
+        const double2 t = *reinterpret_cast<const double2*>(p);
+        v[0] = t.x; v[1] = t.y;
+    }
+    static __device__ __forceinline__ void st(double* p, const double* v) {
+        *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    }
+};
+
+template <typename T, int DIR, int CPT>
 __global__ void __launch_bounds__(256)
 mr_line_yz(const T* __restrict__ P, const T* __restrict__ Vc, Tab<T> tx, Tab<T> ty, Tab<T> tz, MrArgs a,
            T* __restrict__ out) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int nlong = DIR == 1 ? a.ny : a.nz;                 // fine cells along the line
     const int ntr = DIR == 1 ? a.nz : a.ny;                   // second transverse fine size
-    if (t >= (int64_t)a.nx * ntr) return;
-    const int i = (int)(t % a.nx), o = (int)(t / a.nx);       // fine x and the other transverse index
+    const int nxc = a.nx / CPT;                               // column groups along x
+    if (t >= (int64_t)nxc * ntr) return;
+    const int i = (int)(t % nxc) * CPT, o = (int)(t / nxc);   // first fine x and the other transverse index
     const Tab<T>& to = DIR == 1 ? tz : ty;                    // table of the other transverse direction
     const Tab<T>& tl = DIR == 1 ? ty : tz;                    // table along the line
     const int ncl = DIR == 1 ? a.ncy : a.ncz;                 // coarse cells along the line
@@ -427,43 +492,60 @@ mr_line_yz(const T* __restrict__ P, const T* __restrict__ Vc, Tab<T> tx, Tab<T> 
     const T* p0 = DIR == 1 ? P + (int64_t)o * a.ncy * a.nx + i : P + (int64_t)o * a.nx + i;
     const int64_t pst = DIR == 1 ? (int64_t)a.nx : (int64_t)a.ny * a.nx;
     // reference plane: v at y = 0 (plane [kz][0][kx] of Vc) or w at z = 0
-    T ref = T(0);
-    if (!a.wall[DIR]) {
-        T wxv[4], wov[4];
-        load_w(tx.w, i, wxv);
-        load_w(to.w, o, wov);
-        if (DIR == 1)
-            ref = hermite2(Vc, (int64_t)a.ncfy * a.ncx, (int64_t)1, a.ncz, a.ncx, to.s[o], wov, tx.s[i], wxv);
-        else
-            ref = hermite2(Vc, (int64_t)a.ncx, (int64_t)1, a.ncy, a.ncx, to.s[o], wov, tx.s[i], wxv);
+    T ref[CPT];
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+        ref[c] = T(0);
+        if (!a.wall[DIR]) {
+            T wxv[4], wov[4];
+            load_w(tx.w, i + c, wxv);
+            load_w(to.w, o, wov);
+            if (DIR == 1)
+                ref[c] = hermite2(Vc, (int64_t)a.ncfy * a.ncx, (int64_t)1, a.ncz, a.ncx, to.s[o], wov, tx.s[i + c], wxv);
+            else
+                ref[c] = hermite2(Vc, (int64_t)a.ncx, (int64_t)1, a.ncy, a.ncx, to.s[o], wov, tx.s[i + c], wxv);
+        }
     }
-    T win[4];
+    T win[4][CPT];
     int ws = -1;  // coarse start index of the window
     const T hT = (T)a.h;
-    BlockSum<T> run;
+    BlockSum<T> run[CPT];
     int64_t idx = DIR == 1 ? ((int64_t)o * a.nfy) * a.nx + i : (int64_t)o * a.nx + i;
     const int64_t ost = DIR == 1 ? (int64_t)a.nx : (int64_t)a.ny * a.nx;  // output stride along the line
     for (int jl = 0; jl < nlong; ++jl, idx += ost) {
         const int sl = tl.s[jl];
         if (sl != ws) {
             if (ws >= 0 && sl == wrap_add(ws, 1, ncl)) {
-                win[0] = win[1];
-                win[1] = win[2];
-                win[2] = win[3];
-                win[3] = p0[wrap_add(sl, 3, ncl) * pst];
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) {
+                    win[0][c] = win[1][c];
+                    win[1][c] = win[2][c];
+                    win[2][c] = win[3][c];
+                }
+                MrVec<T, CPT>::ld(p0 + wrap_add(sl, 3, ncl) * pst, win[3]);
             } else {
 #pragma unroll
-                for (int m = 0; m < 4; ++m) win[m] = p0[wrap_add(sl, m, ncl) * pst];
+                for (int m = 0; m < 4; ++m) MrVec<T, CPT>::ld(p0 + wrap_add(sl, m, ncl) * pst, win[m]);
             }
             ws = sl;
         }
         T wl[4];
         load_w(tl.w, jl, wl);
-        const T gval = wl[0] * win[0] + wl[1] * win[1] + wl[2] * win[2] + wl[3] * win[3];
-        out[idx] = ref + hT * run.value();
-        run.add(gval);
+        T o_[CPT];
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+            const T gval = wl[0] * win[0][c] + wl[1] * win[1][c] + wl[2] * win[2][c] + wl[3] * win[3][c];
+            o_[c] = ref[c] + hT * run[c].value();
+            run[c].add(gval);
+        }
+        MrVec<T, CPT>::st(out + idx, o_);
     }
-    if (a.wall[DIR]) out[idx] = ref + hT * run.value();
+    if (a.wall[DIR]) {
+        T o_[CPT];
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) o_[c] = ref[c] + hT * run[c].value();
+        MrVec<T, CPT>::st(out + idx, o_);
+    }
 }
 
 MrArgs mr_args(const ch_handle* h) {
@@ -530,21 +612,29 @@ int interp(ch_handle* h, cudaEvent_t* ev = nullptr) {
     }
     T* P = (T*)h->mr_plane;
     const size_t zsm = (size_t)a.ncx * sizeof(T);
+    // the line march with CPT adjacent columns per thread where nx allows
+    constexpr int CPT = sizeof(T) == 4 ? CH_MR_CPT : (CH_MR_CPT < 2 ? CH_MR_CPT : 2);
+    auto line = [&](auto dirc, const T* Vc, T* out, int64_t ntr) {
+        constexpr int DIR = decltype(dirc)::value;
+        if (a.nx % CPT == 0) {
+            const int64_t thr = (int64_t)(a.nx / CPT) * ntr;
+            mr_line_yz<T, DIR, CPT><<<(unsigned)((thr + 255) / 256), 256, 0, h->stream>>>(P, Vc, tx, ty, tz, a, out);
+        } else {
+            const int64_t thr = (int64_t)a.nx * ntr;
+            mr_line_yz<T, DIR, 1><<<(unsigned)((thr + 255) / 256), 256, 0, h->stream>>>(P, Vc, tx, ty, tz, a, out);
+        }
+    };
     {
         mr_plane_yz<T, 1><<<16 * 152, 256, zsm, h->stream>>>((const T*)h->grad_c[1], tx, ty, tz, a, P);
         CHG_CUDA(h, cudaGetLastError());
-        const int64_t thr = (int64_t)a.nx * a.nz;
-        mr_line_yz<T, 1><<<(unsigned)((thr + 255) / 256), 256, 0, h->stream>>>(P, (const T*)h->vel_c[1], tx, ty, tz,
-                                                                               a, (T*)h->vel[1]);
+        line(std::integral_constant<int, 1>{}, (const T*)h->vel_c[1], (T*)h->vel[1], a.nz);
         CHG_CUDA(h, cudaGetLastError());
         if (ev) CHG_CUDA(h, cudaEventRecord(ev[3], h->stream));
     }
     {
         mr_plane_yz<T, 2><<<16 * 152, 256, zsm, h->stream>>>((const T*)h->grad_c[2], tx, ty, tz, a, P);
         CHG_CUDA(h, cudaGetLastError());
-        const int64_t thr = (int64_t)a.nx * a.ny;
-        mr_line_yz<T, 2><<<(unsigned)((thr + 255) / 256), 256, 0, h->stream>>>(P, (const T*)h->vel_c[2], tx, ty, tz,
-                                                                               a, (T*)h->vel[2]);
+        line(std::integral_constant<int, 2>{}, (const T*)h->vel_c[2], (T*)h->vel[2], a.ny);
         CHG_CUDA(h, cudaGetLastError());
         if (ev) CHG_CUDA(h, cudaEventRecord(ev[4], h->stream));
     }

@@ -4,7 +4,8 @@
 multiple-resolution recipe (uniform fine mesh NX x NY x NZ, x/y periodic,
 no-flux z-walls, a tanh-stretched coarse mesh of a quarter of the cells per
 direction with a seeded divergence-free velocity, 20 drops), then runs the
-velocity transfer, two FP32 RK3 steps, the mass and the free energy: every
+velocity transfer, two FP32 RK3 steps, and the mass and free energy in one
+pass (ch_diagnostics): every
 kernel of the hot path launches a few times, on inputs a few hundred MB in
 size, so a one-kernel ncu capture (``-k <name> -c 1``) ends quickly.
 
@@ -39,7 +40,7 @@ def step_case(nx, ny, nz):
         s.interp_to_fine()
         s.step(2)
         b.record(s.stream)
-    m, e = s.mass(), s.free_energy()
+    m, e = s.diagnostics()
     out = dict(case="step", fine=[nx, ny, nz], ms=a.elapsed_time(b), mass=m, free_energy=e)
     s.close()
     return out
