@@ -295,11 +295,14 @@ def test_graph_replay_matches_direct_launches():
 
 
 @pytest.mark.parametrize("shape,bc,prec", [
-    ((6, 600, 8), (co.PERIODIC, co.PERIODIC, co.NOFLUX), "f32"),   # y 600: shared-memory tile solver
-    ((560, 5, 6), (co.NOFLUX, co.NOFLUX, co.PERIODIC), "f32"),     # z 560 periodic + update: tile solver
-    ((6, 300, 10), (co.PERIODIC, co.PERIODIC, co.NOFLUX), "f32"),  # y 300 periodic: cluster of 2
-    ((400, 6, 6), (co.PERIODIC, co.NOFLUX, co.NOFLUX), "f32"),     # z 400 walls + update: cluster of 2
-    ((6, 600, 7), (co.PERIODIC, co.PERIODIC, co.NOFLUX), "f32"),   # odd nx: shared-memory tile solver
+    ((6, 600, 8), (co.PERIODIC, co.PERIODIC, co.NOFLUX), "f32"),   # y 600: 4 lines a warp, ragged 32-column tile
+    ((6, 300, 12), (co.PERIODIC, co.PERIODIC, co.NOFLUX), "f32"),  # y 300 (M = 16): 4 lines a warp
+    ((560, 5, 12), (co.NOFLUX, co.NOFLUX, co.PERIODIC), "f32"),    # z 560 periodic + update: 4 lines a warp
+    ((400, 6, 8), (co.PERIODIC, co.NOFLUX, co.NOFLUX), "f32"),     # z 400 walls + update: 4 lines a warp
+    ((560, 5, 6), (co.NOFLUX, co.NOFLUX, co.PERIODIC), "f32"),     # z 560, nx not a multiple of 4: one-line tile
+    ((6, 300, 10), (co.PERIODIC, co.PERIODIC, co.NOFLUX), "f32"),  # y 300, nx not a multiple of 4: cluster of 2
+    ((400, 6, 6), (co.PERIODIC, co.NOFLUX, co.NOFLUX), "f32"),     # z 400 walls + update, same: cluster of 2
+    ((6, 600, 7), (co.PERIODIC, co.PERIODIC, co.NOFLUX), "f32"),   # odd nx: one-line shared-memory tile
     ((6, 300, 8), (co.PERIODIC, co.PERIODIC, co.NOFLUX), "f64"),   # FP64: one-column form
     ((6, 1024, 8), (co.PERIODIC, co.PERIODIC, co.NOFLUX), "f64"),  # FP64 y 1024: 16-column tile, ragged x edge
     ((1024, 5, 20), (co.NOFLUX, co.PERIODIC, co.NOFLUX), "f64"),   # FP64 z 1024 walls + update: two 16-column tiles
@@ -307,10 +310,13 @@ def test_graph_replay_matches_direct_launches():
     ((150, 200, 34), (co.PERIODIC, co.NOFLUX, co.PERIODIC), "f32"),  # y 200 walls, z 150 periodic + update: 16 warps x 16 rows
 ])
 def test_long_lines(shape, bc, prec):
-    """Lines longer than 256 cells: up to 512, the cluster form of the
-    two-column solver (FP32, even nx) or the one-column form; beyond, the tile
-    solver (16 columns wide for FP64 lines of 1024 cells).  Also ragged 65..256-cell lines on the 16-row shapes of the
-    two-column solver (8 or 16 warps, last warp partly past the line end)."""
+    """Lines longer than 256 cells: FP32 with nx a multiple of 4 takes the
+    multi-line shared-memory solver (4 lines a warp over 32-column tiles,
+    ragged where nx < 32); otherwise the cluster form of the two-column solver
+    (FP32, even nx, up to 512 cells), the one-column form, or the one-line tile
+    solver (16 columns wide for FP64 lines of 1024 cells).  Also ragged
+    65..256-cell lines on the 16-row shapes of the two-column solver (8 or 16
+    warps, last warp partly past the line end)."""
     h = 1.0 / 64
     cn = 0.75 * h
     rng = np.random.default_rng(17)
