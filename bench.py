@@ -548,27 +548,29 @@ class HotPath:
 
 def e2e_pipelined(hps, hostC, outC, steps, dev):
     """`steps` hot-path steps through the public API with host buffers, with
-    the copies overlapped with compute on two solver instances of the same
-    workload: step n runs on instance n % 2, whose C and coarse velocity were
-    copied from pinned host memory (one copy stream) while step n - 1 ran on
-    the other instance; step n's result C is copied back to pinned host memory
-    (a second copy stream) while step n + 1 runs.  Compute stays one step at a
-    time: each step waits for the end of the previous one.  Returns the seconds
-    from the first host-to-device copy to the end of the last device-to-host
-    copy."""
+    the copies overlapped with compute on k = len(hps) solver instances of the
+    same workload: step n runs on instance n % k, whose C and coarse velocity
+    were copied from pinned host memory (one copy stream) while step n - 1
+    ran; step n's result C is copied back to pinned host memory (a second copy
+    stream) while step n + 1 runs.  An instance takes new inputs only once its
+    last result is back on the host, so with k = 3 the two copy directions
+    never wait for each other.  Compute stays one step at a time: each step
+    waits for the end of the previous one.  Returns the seconds from the first
+    host-to-device copy to the end of the last device-to-host copy."""
     import torch
     h2d, d2h = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-    free = [None, None]         # the instance's last result is back on the host
+    k = len(hps)
+    free = [None] * k           # the instance's last result is back on the host
     ready = [None] * steps      # step n's inputs are on the device
     done = [None] * steps       # step n has finished
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
 
     def upload(n):
-        hp = hps[n % 2]
+        hp = hps[n % k]
         with torch.cuda.stream(h2d):
-            if free[n % 2] is not None:
-                h2d.wait_event(free[n % 2])
+            if free[n % k] is not None:
+                h2d.wait_event(free[n % k])
             hp.s.C.copy_(hostC, non_blocking=True)
             for d, s in zip(hp.velc, hp.velc_host):
                 d.copy_(s, non_blocking=True)
@@ -578,7 +580,7 @@ def e2e_pipelined(hps, hostC, outC, steps, dev):
     t0.record(h2d)
     upload(0)
     for n in range(steps):
-        hp = hps[n % 2]
+        hp = hps[n % k]
         st = hp.s.stream
         if n + 1 < steps:
             upload(n + 1)
@@ -591,8 +593,8 @@ def e2e_pipelined(hps, hostC, outC, steps, dev):
         d2h.wait_event(done[n])
         with torch.cuda.stream(d2h):
             outC.copy_(hp.s.C, non_blocking=True)
-            free[n % 2] = torch.cuda.Event()
-            free[n % 2].record(d2h)
+            free[n % k] = torch.cuda.Event()
+            free[n % k].record(d2h)
     t1.record(d2h)
     torch.cuda.synchronize(dev)
     return t0.elapsed_time(t1) / 1e3
@@ -746,15 +748,30 @@ def gpu_arm(args):
     k_e2e = max(3, min(args.steps, 10))
     h2d_bytes = ncell * 4 + sum(t.numel() * 4 for t in hp.velc_host)
     sec_serial = max_ranks(timed(hp, k_e2e, 2, per_step=e2e_step))
-    hp2 = HotPath(f, "f32", dev)  # the second instance of the overlapped form
-    sec_e2e = max_ranks(e2e_pipelined([hp, hp2], hostC, outC, k_e2e, dev))
-    hp2.s.close()
-    del hp2
+    # the host link on its own: one C each way (the overlapped form below is
+    # bound by these when they exceed a step)
+    link = {}
+    for name, fn in (("h2d_gbs", lambda: hp.s.C.copy_(hostC, non_blocking=True)),
+                     ("d2h_gbs", lambda: outC.copy_(hp.s.C, non_blocking=True))):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        with torch.cuda.stream(hp.s.stream):
+            a.record(hp.s.stream)
+            fn()
+            b.record(hp.s.stream)
+        torch.cuda.synchronize(dev)
+        link[name] = ncell * 4 / (a.elapsed_time(b) * 1e-3) / 1e9
+    extra_hp = [HotPath(f, "f32", dev) for _ in range(2)]  # instances 2 and 3 of the overlapped form
+    sec_e2e = max_ranks(e2e_pipelined([hp] + extra_hp, hostC, outC, k_e2e, dev))
+    for x in extra_hp:
+        x.s.close()
+    del extra_hp
     e2e = dict(value=ncell * k_e2e * world / sec_e2e, unit="cell-updates/s", steps=k_e2e,
                h2d_bytes_per_step=h2d_bytes, d2h_bytes_per_step=ncell * 4,
                pipelined=("every step copies its inputs (C and the coarse velocity) from pinned host memory and "
-                          "its result C back; two solver instances alternate, so step n+1's inputs are copied in "
-                          "and step n-1's result is copied out while step n runs (compute one step at a time)"),
+                          "its result C back; three solver instances take turns, so step n+1's inputs are copied "
+                          "in and step n-1's result is copied out while step n runs (compute one step at a time)"),
+               host_link=link,
                serial_value=ncell * k_e2e * world / sec_serial,
                serial="the same copies, not overlapped: H2D, step, D2H in order on one stream")
     launches = hp.launches_per_step()
