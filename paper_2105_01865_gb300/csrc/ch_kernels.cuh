@@ -1251,7 +1251,7 @@ struct YZVShape {
 template <typename T, int M, bool UPDATE, int L, int NC, int MAXB>
 __global__ void __launch_bounds__(NC / L * 32, (YZVShape<T, M, L, NC, MAXB>::kMinBlocks))
 ch_solve_yz_v(T* __restrict__ a, T* __restrict__ Cf, int nx, int64_t outer_stride, int64_t line_stride,
-              WCoef<T> cf, unsigned int* status) {
+              WCoef<T> cf, unsigned int* status, int64_t ntiles) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     pdl_wait();
     pdl_launch_dependents();
@@ -1261,16 +1261,17 @@ ch_solve_yz_v(T* __restrict__ a, T* __restrict__ Cf, int nx, int64_t outer_strid
     T* s = reinterpret_cast<T*>(smem_raw);
     const int n = cf.n;
     const int xblocks = (nx + NC - 1) / NC;
-    const int xb = (int)(blockIdx.x % xblocks);
-    const int64_t outer = blockIdx.x / xblocks;
-    const int i0 = xb * NC;
-    const int nl = min(NC, nx - i0);  // a multiple of L
-    const int64_t base = outer * outer_stride + i0;
     const int tid = threadIdx.x, g = tid % G, rr = tid / G;  // column group g, rows rr, rr + 32, ...
     const int c = g * L;
     auto slot = [&](int j) { return (j / M) * kChunk + (j % M) * NC + c; };
-#pragma unroll 4
-    for (int j = rr; j < 32 * M; j += 32) {
+    // tile t: NC consecutive x (nl of them inside the mesh, a multiple of L) of one outer position
+    auto tile_base = [&](int64_t t, int& nl) {
+        const int i0 = (int)(t % xblocks) * NC;
+        nl = min(NC, nx - i0);
+        return (t / xblocks) * outer_stride + i0;
+    };
+    // this thread's piece of row j of a tile, or zeros past the line or the ragged x edge
+    auto stage_row = [&](int j, int64_t base, int nl) {
         if (j < n && c < nl) {
             cp_async_vec<T, L>(s + slot(j), a + base + (int64_t)j * line_stride + c);
         } else {
@@ -1279,51 +1280,74 @@ ch_solve_yz_v(T* __restrict__ a, T* __restrict__ Cf, int nx, int64_t outer_strid
             for (int q = 0; q < L; ++q) z[q] = T(0);
             vst<T, L>(s + slot(j), z);
         }
-    }
+    };
+    // A CTA takes tiles blockIdx.x, blockIdx.x + gridDim.x, ...  The write-back
+    // of a tile is fused with the staging of the next: each thread re-fills the
+    // slots it has just written out, so the next tile's loads run while the
+    // other threads still store.
+    int64_t t = blockIdx.x;
+    if (t >= ntiles) return;
+    int nl;
+    int64_t base = tile_base(t, nl);
+#pragma unroll 4
+    for (int j = rr; j < 32 * M; j += 32) stage_row(j, base, nl);
     cp_async_commit();
-    cp_async_wait<0>();
-    __syncthreads();
     const int warp = tid >> 5, lane = tid & 31;
-    warp_lines_solve_smv<T, M, L>(s + (size_t)lane * kChunk + warp * L, NC, cf, lane);
-    __syncthreads();
     bool bad = false;
-    if constexpr (UPDATE) {
-        // rows rr + 32 t (t < M) in batches of 8: the batch's C loads are all
-        // issued before its first store (a store to C would otherwise hold
-        // back the next row's load)
-        constexpr int kB = M < 8 ? M : 8;
+    for (;;) {
+        cp_async_wait<0>();
+        __syncthreads();
+        warp_lines_solve_smv<T, M, L>(s + (size_t)lane * kChunk + warp * L, NC, cf, lane);
+        __syncthreads();
+        const int64_t tn = t + gridDim.x;
+        const bool more = tn < ntiles;
+        int nln = 0;
+        const int64_t basen = more ? tile_base(tn, nln) : 0;
+        if constexpr (UPDATE) {
+            // rows rr + 32 u (u < M) in batches of 8: the batch's C loads are
+            // all issued before its first store (a store to C would otherwise
+            // hold back the next row's load)
+            constexpr int kB = M < 8 ? M : 8;
 #pragma unroll 1
-        for (int t0 = 0; t0 < M; t0 += kB) {
-            T cv[kB][L];
+            for (int u0 = 0; u0 < M; u0 += kB) {
+                T cv[kB][L];
 #pragma unroll
-            for (int t = 0; t < kB; ++t) {
-                const int j = rr + 32 * (t0 + t);
-                if (j < n && c < nl) vld<T, L>(Cf + base + (int64_t)j * line_stride + c, cv[t]);
+                for (int u = 0; u < kB; ++u) {
+                    const int j = rr + 32 * (u0 + u);
+                    if (j < n && c < nl) vld<T, L>(Cf + base + (int64_t)j * line_stride + c, cv[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < kB; ++u) {
+                    const int j = rr + 32 * (u0 + u);
+                    if (j < n && c < nl) {
+                        T d[L];
+                        vld<T, L>(s + slot(j), d);
+#pragma unroll
+                        for (int q = 0; q < L; ++q) {
+                            cv[u][q] += d[q];
+                            bad |= !isfinite(cv[u][q]);
+                        }
+                        vst<T, L>(Cf + base + (int64_t)j * line_stride + c, cv[u]);
+                    }
+                    if (more) stage_row(j, basen, nln);
+                }
             }
-#pragma unroll
-            for (int t = 0; t < kB; ++t) {
-                const int j = rr + 32 * (t0 + t);
+        } else {
+#pragma unroll 4
+            for (int j = rr; j < 32 * M; j += 32) {
                 if (j < n && c < nl) {
                     T d[L];
                     vld<T, L>(s + slot(j), d);
-#pragma unroll
-                    for (int q = 0; q < L; ++q) {
-                        cv[t][q] += d[q];
-                        bad |= !isfinite(cv[t][q]);
-                    }
-                    vst<T, L>(Cf + base + (int64_t)j * line_stride + c, cv[t]);
+                    vst<T, L>(a + base + (int64_t)j * line_stride + c, d);
                 }
+                if (more) stage_row(j, basen, nln);
             }
         }
-    } else {
-#pragma unroll 4
-        for (int j = rr; j < n; j += 32) {
-            if (c < nl) {
-                T d[L];
-                vld<T, L>(s + slot(j), d);
-                vst<T, L>(a + base + (int64_t)j * line_stride + c, d);
-            }
-        }
+        if (!more) break;
+        cp_async_commit();
+        t = tn;
+        base = basen;
+        nl = nln;
     }
     if (UPDATE && bad) atomicOr(status, 1u);
 }
@@ -1621,6 +1645,11 @@ __global__ void __launch_bounds__(256) ch_add_increment(T* __restrict__ C, const
 // single-block pass in fixed order, so results are deterministic.
 // ---------------------------------------------------------------------------
 constexpr int kRedThreads = 256;
+// 128-cell chunks of a row in flight per warp in the free-energy pass
+#ifndef CH_RED_UNROLL
+#define CH_RED_UNROLL 2
+#endif
+constexpr int kRedUnroll = CH_RED_UNROLL;
 
 __device__ __forceinline__ double block_sum(double v) {
     __shared__ double ws[kRedThreads / 32];
@@ -1723,7 +1752,7 @@ ch_reduce_energy(const T* __restrict__ C, int nx, int ny, int nz, int bcx, int b
                 // relative size 2^-24) and the sum enters the compensated
                 // accumulator once; the mass adds every C compensated, as
                 // ch_reduce_mass does
-#pragma unroll 2
+#pragma unroll kRedUnroll
                 for (int i0 = 4 * lane; i0 < nx; i0 += 128) {
                     const float4 c4 = *reinterpret_cast<const float4*>(p + i0);
                     const float4 y4 = *reinterpret_cast<const float4*>(py + i0);

@@ -79,7 +79,18 @@ constexpr size_t kMaxSmem = 227 * 1024;  // dynamic shared memory per CTA (sm_10
 #ifndef CH_X_WARPS
 #define CH_X_WARPS 2
 #endif
+// y/z multi-line tiles from persistent CTAs, each tile's write-back fused
+// with the staging of the CTA's next tile (0: one CTA per tile, the default:
+// the persistent form measured slower, y 1.47 against 1.41 ms and z 1.41
+// against 1.38 ms on the 1024x1024x512 mesh)
+#ifndef CH_YZ_PERSIST
+#define CH_YZ_PERSIST 0
+#endif
 // shortest lines (in rows per lane, M) that take the multi-line solvers
+// CTAs per SM of the mass and free-energy reductions
+#ifndef CH_RED_BLOCKS_PER_SM
+#define CH_RED_BLOCKS_PER_SM 4
+#endif
 #ifndef CH_MULTI_MIN_M
 #define CH_MULTI_MIN_M 16
 #endif
@@ -236,17 +247,24 @@ template <typename T, int M, int L, int NC, int B>
 void launch_yz_v(ch_handle* h, int dir, T* r, T* Cupd, const WCoef<T>& cf) {
     using S = YZVShape<T, M, L, NC, B>;
     const int nx = (int)h->n[0], ny = (int)h->n[1], nz = (int)h->n[2];
-    const unsigned xblocks = (unsigned)((nx + NC - 1) / NC);
+    const int64_t xblocks = (nx + NC - 1) / NC;
     const int64_t plane = (int64_t)nx * ny;
+    const int64_t ntiles = xblocks * (dir == 1 ? nz : ny);
+    // persistent CTAs (each runs tiles blockIdx.x, + gridDim.x, ...): as many
+    // as fit on the device at once
+    int dev = 0, nsm = 152;
+    if (CH_YZ_PERSIST && cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned grid = (unsigned)(CH_YZ_PERSIST ? std::min<int64_t>(ntiles, (int64_t)S::kMinBlocks * nsm) : ntiles);
     if (dir == 1)
-        launch_k(h->stream, ch_solve_yz_v<T, M, false, L, NC, B>, dim3(xblocks * (unsigned)nz), dim3(S::kWarps * 32),
-                 S::kTileBytes, r, nullptr, nx, plane, (int64_t)nx, cf, h->status);
+        launch_k(h->stream, ch_solve_yz_v<T, M, false, L, NC, B>, dim3(grid), dim3(S::kWarps * 32), S::kTileBytes, r,
+                 nullptr, nx, plane, (int64_t)nx, cf, h->status, ntiles);
     else if (Cupd)
-        launch_k(h->stream, ch_solve_yz_v<T, M, true, L, NC, B>, dim3(xblocks * (unsigned)ny), dim3(S::kWarps * 32),
-                 S::kTileBytes, r, Cupd, nx, (int64_t)nx, plane, cf, h->status);
+        launch_k(h->stream, ch_solve_yz_v<T, M, true, L, NC, B>, dim3(grid), dim3(S::kWarps * 32), S::kTileBytes, r,
+                 Cupd, nx, (int64_t)nx, plane, cf, h->status, ntiles);
     else
-        launch_k(h->stream, ch_solve_yz_v<T, M, false, L, NC, B>, dim3(xblocks * (unsigned)ny), dim3(S::kWarps * 32),
-                 S::kTileBytes, r, nullptr, nx, (int64_t)nx, plane, cf, h->status);
+        launch_k(h->stream, ch_solve_yz_v<T, M, false, L, NC, B>, dim3(grid), dim3(S::kWarps * 32), S::kTileBytes, r,
+                 nullptr, nx, (int64_t)nx, plane, cf, h->status, ntiles);
 }
 
 // Whether FP32 lines of 257..1024 cells (M = 16, 32) along dir go through the
@@ -875,7 +893,7 @@ int ch_create(const ch_params* p, void* C, void* work, size_t work_bytes, void* 
         if (cudaMemcpy(h->coef_buf, host.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) rc = CH_ECUDA;
     }
     if (rc == CH_OK) {
-        h->red_blocks = 4 * 152;
+        h->red_blocks = CH_RED_BLOCKS_PER_SM * 152;
         if (cudaMalloc(&h->red_partials, 2 * (size_t)h->red_blocks * sizeof(double)) != cudaSuccess ||
             cudaMalloc(&h->red_out, 2 * sizeof(double)) != cudaSuccess ||
             cudaMalloc(&h->status, sizeof(unsigned int)) != cudaSuccess)
