@@ -9,6 +9,9 @@ pass (ch_diagnostics): every
 kernel of the hot path launches a few times, on inputs a few hundred MB in
 size, so a one-kernel ncu capture (``-k <name> -c 1``) ends quickly.
 
+``python -m paper_2105_01865_gb300.profile_case restrict NX NY NZ`` runs the
+down-sampling of the fine fields to the coarse mesh of the same recipe twice.
+
 ``python -m paper_2105_01865_gb300.profile_case batch NBOX MODE`` runs two
 steps of the first NBOX boxes of the batched workload (64 uneven periodic
 boxes, u = 0) with the persistent (MODE = persistent) or per-phase
@@ -46,6 +49,29 @@ def step_case(nx, ny, nz):
     return out
 
 
+def restrict_case(nx, ny, nz):
+    """The down-sampling of the fine C to the coarse mesh (C, rho, mu, F_st) on
+    the step case's recipe, twice."""
+    import torch
+
+    from . import build, capi, inputs
+    from .solver import Solver
+    build.build()
+    capi.load()
+    f = inputs.multires_box((nx, ny, nz), (max(nx // 4, 4), max(ny // 4, 4), max(nz // 4, 4)), 20)
+    s = Solver(f["shape"], f["h"], f["bc"], f["cn"], f["pe"], 1e-4, f["C"], precision="f32", coarse_faces=f["faces"])
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.restrict_to_coarse(0.05, 1.0)
+    with torch.cuda.stream(s.stream):
+        a.record(s.stream)
+        s.restrict_to_coarse(0.05, 1.0)
+        b.record(s.stream)
+    s.sync()
+    out = dict(case="restrict", fine=[nx, ny, nz], ms=a.elapsed_time(b))
+    s.close()
+    return out
+
+
 def batch_case(nbox, mode):
     import numpy as np
     import torch
@@ -74,6 +100,8 @@ def batch_case(nbox, mode):
 def main(argv):
     if len(argv) >= 4 and argv[0] == "step":
         print(json.dumps(step_case(int(argv[1]), int(argv[2]), int(argv[3]))))
+    elif len(argv) >= 4 and argv[0] == "restrict":
+        print(json.dumps(restrict_case(int(argv[1]), int(argv[2]), int(argv[3]))))
     elif len(argv) >= 3 and argv[0] == "batch":
         print(json.dumps(batch_case(int(argv[1]), argv[2])))
     else:
