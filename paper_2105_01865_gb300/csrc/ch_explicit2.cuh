@@ -9,6 +9,8 @@
 // global accesses become 8-byte (float2) or 16-byte (double2) vectors.
 #pragma once
 
+#include <cuda.h>
+
 #include "ch_kernels.cuh"
 
 namespace chg {
@@ -173,6 +175,9 @@ __device__ __forceinline__ Pr<T> face_flux_p(Pr<T> vel, Pr<T> m3, Pr<T> m2, Pr<T
 #ifndef CH_EXPLICIT_STAGE_OFFSETS
 #define CH_EXPLICIT_STAGE_OFFSETS 1
 #endif
+#ifndef CH_EXPLICIT_TMA_RECOMPUTE
+#define CH_EXPLICIT_TMA_RECOMPUTE 1
+#endif
 #ifndef CH_EXPLICIT_PREFETCH
 #define CH_EXPLICIT_PREFETCH 1
 #endif
@@ -196,17 +201,29 @@ inline int explicit_zchunk(int nx, int ny, int nz, bool fp32) {
 // One 64 x 8 x zchunk tile (tile coordinates bx, by, bz) computed by the 256
 // threads of a CTA; called by the standalone kernel below and by the batched
 // persistent kernel.
-template <typename T, bool ADV, bool DIRI = false>
+template <typename T, bool ADV, bool DIRI = false, bool TMA = false>
 // DIRI: compiled for Dirichlet z-walls (negated ghost planes); false for every
 // other wall type, which then carries no extra code.
+// TMA (FP32): tiles whose 72 x 14 staged plane needs no wrapped or mirrored
+// index are staged by one tensor-map tile load per plane (tmap: a 3D map of C
+// with a 72 x 14 x 1 box), completed on a shared-memory mbarrier; the others
+// stage element by element.  A wait that gives up sets bit 4 of *status
+// (the launch's results are then void).
 // Data pointers carry no __restrict__ here: the batched persistent kernel
 // writes these arrays in one phase and reads them in the next, so their loads
 // must not go through the non-coherent read-only path.
 __device__ __forceinline__ void explicit_tile2(const T* C, const T* u, const T* v, const T* w, const T* Hprev,
                                                T* Hout, T* r, const RhsArgs<T>& a, int bx, int by, int bz,
-                                               int zchunk) {
+                                               int zchunk, const void* tmap = nullptr,
+                                               unsigned int* status = nullptr) {
     constexpr int PX = kTX2 + 2 * kHL2, PY = kTY + 2 * kHalo;  // 72 x 14
-    __shared__ __align__(16) T Cs[3][PY][PX];
+    // with TMA every buffer starts on a 128-byte boundary (16 rows of 288 B)
+    constexpr int PYB = TMA ? 16 : PY;
+    // ring of staged planes: 3 (one plane ahead), 4 with TMA (tile loads two
+    // planes ahead; element staging stays one ahead)
+    constexpr int NB = TMA ? 4 : 3;
+    __shared__ __align__(128) T Cs[NB][PYB][PX];
+    __shared__ __align__(8) unsigned long long mbar[TMA ? NB : 1];
     __shared__ __align__(16) T Fx[ADV ? kTY : 1][kTX2 + 2];
     __shared__ __align__(16) T Fy[ADV ? kTY + 1 : 1][kTX2];
     __shared__ int gi_tab[PX], gj_tab[PY];
@@ -233,6 +250,17 @@ __device__ __forceinline__ void explicit_tile2(const T* C, const T* u, const T* 
     const int kend = min(k0 + zchunk, a.nz);
 
     __syncthreads();  // the tables and buffers may still be read by a previous tile of this CTA
+    bool use_tma = false;
+    if constexpr (TMA) {
+        static_assert(sizeof(T) == 4, "tensor-map staging is FP32");
+        use_tma = tmap != nullptr && i0 >= kHL2 && i0 + kTX2 + kHL2 <= a.nx && j0 >= kHalo &&
+                  j0 + kTY + kHalo <= a.ny;
+        if (use_tma && tid == 0) {
+#pragma unroll
+            for (int b = 0; b < NB; ++b) mbar_init(&mbar[b], 1);
+            mbar_init_fence();
+        }
+    }
     if (tid < PX) gi_tab[tid] = bc_index(i0 + tid - kHL2, a.nx, a.bcx);
     else if (tid < PX + PY) gj_tab[tid - PX] = bc_index(j0 + (tid - PX) - kHalo, a.ny, a.bcy);
 
@@ -300,42 +328,76 @@ __device__ __forceinline__ void explicit_tile2(const T* C, const T* u, const T* 
     // in-plane source offsets of this thread's staged elements e = tid + 256 m,
     // the same for every plane of the tile
     constexpr int kStageN = (PX * PY + 32 * kTY - 1) / (32 * kTY);
-    int soff[kStageN];
-#pragma unroll
-    for (int m = 0; m < kStageN; ++m) {
-        const int e = tid + m * 32 * kTY;
-        const int row = e / PX, cc = e - row * PX;
-        soff[m] = e < PX * PY ? gj_tab[row] * a.nx + gi_tab[cc] : 0;
-    }
-    auto stage = [&](int kk, int b) {
-        const T* Ck = C + kk * plane;
-        T* dst = &Cs[b][0][0];
+    // with tensor-map staging the element path (edge tiles only) re-derives
+    // its offsets from the tables instead of holding them (CH_EXPLICIT_TMA_RECOMPUTE)
+    constexpr bool kRecompute = TMA && CH_EXPLICIT_TMA_RECOMPUTE;
+    int soff[kRecompute ? 1 : kStageN];
+    if constexpr (!kRecompute) {
 #pragma unroll
         for (int m = 0; m < kStageN; ++m) {
             const int e = tid + m * 32 * kTY;
-            if (e < PX * PY) cp_async_elem(dst + e, Ck + soff[m]);
+            const int row = e / PX, cc = e - row * PX;
+            soff[m] = e < PX * PY ? gj_tab[row] * a.nx + gi_tab[cc] : 0;
         }
-        prefetch(kk);
-        cp_async_commit();
+    }
+    // plane kk of C into buffer b: a tile load (TMA tiles) or per-thread copies
+    auto stage_c = [&](int kk, int b) {
+        const T* Ck = C + kk * plane;
+        T* dst = &Cs[b][0][0];
+        if (TMA && use_tma) {
+            if (tid == 0) {
+                mbar_expect_tx(&mbar[b], (unsigned)(PX * PY * sizeof(T)));
+                tma_load_3d(dst, tmap, i0 - kHL2, j0 - kHalo, kk, &mbar[b]);
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < kStageN; ++m) {
+                const int e = tid + m * 32 * kTY;
+                if constexpr (kRecompute) {
+                    const int row = e / PX, cc = e - row * PX;
+                    if (e < PX * PY) cp_async_elem(dst + e, Ck + (gj_tab[row] * a.nx + gi_tab[cc]));
+                } else {
+                    if (e < PX * PY) cp_async_elem(dst + e, Ck + soff[m]);
+                }
+            }
+        }
     };
 #else
-    auto stage = [&](int kk, int b) {
+    auto stage_c = [&](int kk, int b) {
         const T* Ck = C + (int64_t)kk * plane;
         for (int e = tid; e < PX * PY; e += 32 * kTY) {
             const int row = e / PX, cc = e - row * PX;
             cp_async_elem(&Cs[b][row][cc], Ck + (int64_t)gj_tab[row] * a.nx + gi_tab[cc]);
         }
+    };
+#endif
+    // one commit group per plane: its C (per-thread copies) and its velocity
+    // and H^{l-1} slots
+    auto stage_rest = [&](int kk) {
         prefetch(kk);
         cp_async_commit();
     };
-#endif
-    stage(k0, 0);
-    for (int k = k0, buf = 0; k < kend; ++k, buf = (buf == 2 ? 0 : buf + 1)) {
+    const bool tma_tile = TMA && use_tma;
+    stage_c(k0, 0);
+    if (tma_tile && k0 + 1 < kend) stage_c(k0 + 1, 1);
+    stage_rest(k0);
+    for (int k = k0, buf = 0, it = 0; k < kend; ++k, ++it, buf = (buf + 1 == NB ? 0 : buf + 1)) {
+        const int b1 = buf + 1 == NB ? 0 : buf + 1;
+        if (tma_tile && k + 2 < kend) stage_c(k + 2, b1 + 1 == NB ? 0 : b1 + 1);
         if (k + 1 < kend) {
-            stage(k + 1, buf == 2 ? 0 : buf + 1);
+            if (!tma_tile) stage_c(k + 1, b1);
+            stage_rest(k + 1);
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
+        }
+        if constexpr (TMA) {
+            static_assert(!TMA || CH_EXPLICIT_STAGE_OFFSETS, "tensor-map staging uses the offset-table stage");
+            // buffer buf's it / NB-th fill.  A wait that gives up (after
+            // 2 s) flags the launch and goes on: the results are void then,
+            // and every thread still meets every barrier of the tile.
+            if (use_tma && !mbar_wait_bounded(&mbar[buf], (unsigned)((it / NB) & 1), 2000000000ull) && status)
+                atomicOr(status, 4u);
         }
         // per-thread global inputs of this plane (issued before the barrier)
         Pr<T> qnext = ldp(C + (bc_near(k + 4, a.nz, a.bcz) * plane + col));
@@ -463,15 +525,17 @@ __device__ __forceinline__ void explicit_tile2(const T* C, const T* u, const T* 
 }
 
 // TZ: z-planes per CTA, a compile-time constant (a runtime depth cost 2 % on
-// the 256 x 256 x 128 shear drop).
-template <typename T, bool ADV, bool DIRI, int TZ>
+// the 256 x 256 x 128 shear drop).  TMA: stage C through the tensor map tmap
+// (of this C) where a tile allows.
+template <typename T, bool ADV, bool DIRI, int TZ, bool TMA>
 __global__ void __launch_bounds__(32 * kTY, sizeof(T) == 4 ? CH_EXPLICIT_MIN_BLOCKS : 2)
 ch_explicit_rhs2(const T* __restrict__ C, const T* __restrict__ u, const T* __restrict__ v,
                  const T* __restrict__ w, const T* __restrict__ Hprev, T* __restrict__ Hout, T* __restrict__ r,
-                 RhsArgs<T> a) {
+                 RhsArgs<T> a, const __grid_constant__ CUtensorMap tmap, unsigned int* status) {
     pdl_wait();
     pdl_launch_dependents();
-    explicit_tile2<T, ADV, DIRI>(C, u, v, w, Hprev, Hout, r, a, blockIdx.x, blockIdx.y, blockIdx.z, TZ);
+    explicit_tile2<T, ADV, DIRI, TMA>(C, u, v, w, Hprev, Hout, r, a, blockIdx.x, blockIdx.y, blockIdx.z, TZ,
+                                      TMA ? (const void*)&tmap : nullptr, status);
 }
 
 }  // namespace chg

@@ -73,6 +73,10 @@ struct ch_handle {
     cudaGraphExec_t graph;
     int graph_ready;
     int launches_per_step;
+    // FP32: a 3D tensor map of C with a 72 x 14 x 1 box for the explicit
+    // kernel's tile loads (the bytes of a CUtensorMap; tmap_ok when encoded)
+    unsigned char tmap_c[128];
+    int tmap_ok;
     char err[512];
 };
 
