@@ -196,7 +196,10 @@ int ch_free_energy(ch_handle* h, double* out);
  * CH_ENONFINITE (a NaN/Inf in C), CH_ECUDA. */
 int ch_diagnostics(ch_handle* h, double* mass, double* free_energy);
 
-/* Wait for the handle's stream and report (then clear) the non-finite flag. */
+/* Wait for the handle's stream and report (then clear) the non-finite flag
+ * (CH_ENONFINITE).  A library built with the explicit kernel's tensor-map
+ * staging (CH_EXPLICIT_TMA, off by default) also reports CH_ETIMEOUT when a
+ * tile load did not complete within 2 s; the step's results are then void. */
 int ch_sync(ch_handle* h);
 
 /* Number of kernel launches one ch_step(h, 1) enqueues. */
