@@ -31,8 +31,8 @@
  *    (LU factors, Hermite tables, reduction partials, a status word), freed
  *    by ch_free().
  *  - All work is enqueued on the stream given to ch_create (a cudaStream_t,
- *    NULL = legacy default stream).  Only ch_mass, ch_free_energy, ch_sync
- *    and ch_get_interp_tables wait for the stream.
+ *    NULL = legacy default stream).  Only ch_mass, ch_free_energy,
+ *    ch_diagnostics, ch_sync and ch_get_interp_tables wait for the stream.
  */
 #ifndef CH_GB300_H
 #define CH_GB300_H
