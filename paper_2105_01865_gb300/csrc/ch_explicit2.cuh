@@ -170,7 +170,7 @@ __device__ __forceinline__ Pr<T> face_flux_p(Pr<T> vel, Pr<T> m3, Pr<T> m2, Pr<T
 #define CH_EXPLICIT_TZ 10
 #endif
 #ifndef CH_EXPLICIT_TZ_DEEP
-#define CH_EXPLICIT_TZ_DEEP 32
+#define CH_EXPLICIT_TZ_DEEP 64
 #endif
 #ifndef CH_EXPLICIT_STAGE_OFFSETS
 #define CH_EXPLICIT_STAGE_OFFSETS 1

@@ -420,12 +420,12 @@ def test_fp32_error_per_field_and_step_count(case, hbar):
 
 
 def test_deep_explicit_tiles_ragged_z_fp32_against_fp64():
-    """The 1024 x 512 x 120 shear drop: enough CTAs that the FP32 explicit
-    kernel marches 32-plane tiles (at least 8 waves on the device), the last
-    one 24 planes deep; the FP64 path marches 10-plane tiles and is pinned to
+    """The 1024 x 1024 x 100 shear drop: enough CTAs that the FP32 explicit
+    kernel marches 64-plane tiles (at least 8 waves on the device), the last
+    one 36 planes deep; the FP64 path marches 10-plane tiles and is pinned to
     the oracle on the smaller cases.  Relative L2 and element bars on C after
     2 steps, and mass conservation."""
-    f = inputs.shear_drop_box(1024, 512, 120)
+    f = inputs.shear_drop_box(1024, 1024, 100)
     h = f["h"]
     dt = min(0.9 * stability.stable_dt(f["shape"], h, f["bc"], f["cn"], f["pe"]), 0.5 * h / 0.5)
     S = {p: make(f["shape"], h, f["bc"], f["cn"], f["pe"], dt, f["C"], p, vel=f["vel"]) for p in ("f32", "f64")}
@@ -433,7 +433,7 @@ def test_deep_explicit_tiles_ragged_z_fp32_against_fp64():
     for s in S.values():
         s.step(2)
         s.sync()
-    assert_parity(S["f32"].field(), S["f64"].field(), 1e-6, "1024x512x120 shear drop, FP32 (32-plane tiles) vs FP64")
+    assert_parity(S["f32"].field(), S["f64"].field(), 1e-6, "1024x1024x100 shear drop, FP32 (64-plane tiles) vs FP64")
     for p, s in S.items():
         assert abs(s.mass() - m0[p]) <= (1e-6 if p == "f32" else 1e-12) * abs(m0[p])
         s.close()
